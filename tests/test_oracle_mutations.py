@@ -1,0 +1,108 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each case patches one plausible error into a copy of an oracle routine and checks that
+the corresponding pin of test_oracle_pins.py then fails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import householder as hh
+from oracle import kernels as kk
+from oracle import lowrank as lr
+from oracle import omega as om
+from oracle import sketch as sk
+from oracle import tsqr as ts
+
+
+def _dense_check(f, O, Y, tau):
+    n = Y.shape[0]
+    A = synth.rhs(n, 2, 1).astype(np.float64)
+    Kt = tau * np.eye(n) + Y @ np.linalg.solve(O.T @ Y, Y.T)
+    Xd = np.linalg.solve(Kt, A)
+    return np.linalg.norm(lr.solve(f, A) - Xd) / np.linalg.norm(Xd) < 1e-6
+
+
+def _setup(n=256, d=32, tau=1e-4):
+    pts = synth.points(n, 2, 0).astype(np.float64)
+    O = om.omega_matrix(n, d, 0)
+    Y = sk.sketch(pts, kk.SE, 0.2, 1.0, O)
+    return O, Y, tau
+
+
+def test_unmutated_factor_passes():
+    O, Y, tau = _setup()
+    assert _dense_check(lr.factorise(Y, O, tau, 64), O, Y, tau)
+
+
+def test_dropped_nugget_term_in_core_is_caught():
+    O, Y, tau = _setup()
+    f = lr.factorise(Y, O, tau, 64)
+    f.Cp = f.R.T.copy()                       # mistake: C' = R^T (tau B dropped)
+    f.lu_C = lr.lu_factor(f.Cp)
+    assert not _dense_check(f, O, Y, tau)
+
+
+def test_transposed_b_is_caught():
+    O, Y, tau = _setup()
+    f = lr.factorise(Y, O, tau, 64)
+    f.B = f.Q.T @ O                           # mistake: Q^T Omega instead of Omega^T Q
+    f.Cp = f.R.T + tau * f.B
+    f.lu_B, f.lu_C = lr.lu_factor(f.B), lr.lu_factor(f.Cp)
+    assert not _dense_check(f, O, Y, tau)
+
+
+def test_wrong_hadamard_pattern_is_caught(monkeypatch):
+    def bad(k, p):
+        k = np.asarray(k, dtype=np.uint64)
+        p = np.asarray(p, dtype=np.uint64)
+        return np.where((np.bitwise_count(k | p) & np.uint8(1)) == 0, 1.0, -1.0)
+    monkeypatch.setattr(om, "hadamard_entries", bad)
+    k = np.arange(8, dtype=np.uint64)
+    H = om.hadamard_entries(k[:, None], k[None, :])
+    Hs = np.array([[1.0, 1.0], [1.0, -1.0]])
+    while Hs.shape[0] < 8:
+        Hs = np.block([[Hs, Hs], [Hs, -Hs]])
+    assert not np.array_equal(H, Hs)
+
+
+def test_swapped_tree_children_are_caught(monkeypatch):
+    real = hh.householder_qr
+
+    def swapped(A):
+        m = A.shape[0]
+        if m == 2 * A.shape[1]:               # a tree combine: stack in the wrong order
+            d = A.shape[1]
+            return real(np.vstack([A[d:], A[:d]]))
+        return real(A)
+    monkeypatch.setattr(ts, "householder_qr", swapped)
+    Y = np.random.default_rng(0).standard_normal((256, 16))
+    t = ts.tsqr(Y, 64)
+    Q, R = hh.qr(Y)
+    assert np.abs(t["Q"] - Q).max() > 1e-3
+
+
+def test_dropped_half_in_gradient_is_caught(monkeypatch):
+    n, d = 256, 24
+    pts = synth.points(n, 2, 1).astype(np.float64)
+    y = synth.gp_targets(pts, 0.2, 1.0, 1e-3, seed=1).astype(np.float64)
+
+    def bad_grad(f, yy, Y, Yp, alpha):
+        Q = f.Q
+        KiQ = lr.solve(f, Q)
+        PQ = KiQ - np.outer(alpha, alpha @ Q)
+        QtPQ = Q.T @ PQ
+        PQBi = lr.lu_solve_t(f.lu_B, PQ.T).T
+        M = lr.lu_solve_t(f.lu_B, lr.lu_solve_t(f.lu_B, QtPQ.T).T)
+        Ybar = PQBi - f.omega @ M                 # mistake: the 1/2 is missing
+        return np.array([np.sum(Ybar * Yp), np.sum(Ybar * Y), 0.0]), Ybar
+    monkeypatch.setattr(lr, "grad", bad_grad)
+
+    def F(a):
+        return lr.nll_grad(pts, y, kk.SE, math.exp(a), 1.0, 1e-3, d, 3, 64)
+    h = 1e-4
+    _, g = F(math.log(0.25))
+    fd = (F(math.log(0.25) + h)[0] - F(math.log(0.25) - h)[0]) / (2 * h)
+    assert abs(g[0] - fd) > 1e-3 * abs(fd)
