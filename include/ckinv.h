@@ -1,0 +1,204 @@
+/*
+ * ckinv.h -- C ABI of the GB300 (sm_103a) library for low-rank K^-1 A with a huge,
+ * nearly rank-deficient covariance matrix K, after Banerjee, Vogelstein & Dunson,
+ * "Parallel inversion of huge covariance matrices" (arXiv:1312.1869).
+ *
+ * The paper's problem statement (Sec. 1): evaluate K^-1 A for a symmetric positive
+ * definite K of huge order n without forming K^-1, through a QR decomposition,
+ * R^-1 Q^T A.  Its method (Sec. 3) has three steps, each an entry point here:
+ *   ckinv_sketch  Y = K0 Omega with the structured random Omega = c R T P of
+ *                 Definition 1 (Sec. 3.2), T the Walsh-Hadamard matrix (Sec. 3.2);
+ *   ckinv_tsqr    blocked tall-skinny QR of Y: per-block Householder QR (Eq. 1) and a
+ *                 binary tree of QRs of stacked R factors (Eqs. 2-4);
+ *   ckinv_solve   the low-rank solve that applies Q_hat and R to A.
+ * ckinv_nll_grad evaluates the Gaussian negative log-likelihood and its gradient, the
+ * use the paper targets (Abstract; Sec. 1: "evaluating Gaussian likelihoods").
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major; "ld" is the leading dimension in elements.
+ *   - Array arguments are DEVICE pointers unless the comment says "host"; the caller
+ *     owns them.  ckinv_kinv_a also accepts host pointers (it stages them).
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream) unless they
+ *     return host scalars, which they do after synchronising that stream.
+ *   - Every call returns a ckinv_status and never aborts; ckinv_last_error() gives a
+ *     one-line description of the last failure on that context.
+ *   - A context is not thread-safe: use one per host thread.
+ *
+ * Definitions used throughout (the paper writes no nugget; see DESIGN notes):
+ *   K0 = variance * rho(x_i, x_k)      noise-free kernel matrix,  rho(0) = 1
+ *   Omega[k, j] = c r_k (-1)^popcount(k & p_j),  c = N^-1/2, N = 2^ceil(log2 n)
+ *   Y = K0 Omega = Q_hat R  (diag(R) >= 0),  B = Omega^T Q_hat,  C' = R^T + tau B
+ *   K_tilde = tau I + Y (Omega^T Y)^-1 Y^T        (tau = nugget)
+ *   ckinv_solve returns K_tilde^-1 A = tau^-1 (A - Q_hat C'^-1 R^T Q_hat^T A).
+ */
+#ifndef CKINV_H
+#define CKINV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so that the header needs no CUDA headers. */
+typedef struct CUstream_st *ckinv_stream;
+
+typedef enum {
+  CKINV_OK = 0,
+  CKINV_EINVAL = 1,        /* invalid argument (sizes, null pointers, enum values) */
+  CKINV_ENOMEM = 2,        /* device allocation failed */
+  CKINV_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+  CKINV_ESINGULAR = 4,     /* a zero pivot in an LU factorisation */
+  CKINV_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
+  CKINV_EUNSUPPORTED = 6   /* valid but unsupported here (device, size limit) */
+} ckinv_status;
+
+typedef enum {
+  CKINV_SE = 0,            /* rho = exp(-r^2 / (2 l^2)) */
+  CKINV_MATERN52 = 1,      /* rho = (1 + sqrt5 r/l + 5 r^2/(3 l^2)) exp(-sqrt5 r/l) */
+  CKINV_DENSE = 2          /* K0 is given as a materialised n x n matrix */
+} ckinv_kernel_kind;
+
+typedef enum {
+  CKINV_FP32 = 0,          /* kernel tile x Omega in FP32 FMA (SIMT) */
+  CKINV_BF16 = 1,          /* one BF16 tensor-core product, FP32 accumulation */
+  CKINV_BF16X2 = 2,        /* kernel tile split in two BF16 terms (two products) */
+  CKINV_BF16X3 = 3         /* three BF16 terms: FP32-accurate on tensor cores */
+} ckinv_precision;
+
+typedef struct {
+  int32_t kind;            /* ckinv_kernel_kind */
+  int32_t reserved;        /* must be 0 */
+  double lengthscale;      /* l > 0 (ignored for CKINV_DENSE) */
+  double variance;         /* sigma^2 > 0 (ignored for CKINV_DENSE) */
+  double nugget;           /* tau > 0 */
+} ckinv_kernel;
+
+typedef struct {
+  int64_t n;               /* number of points, n >= d */
+  int32_t dim;             /* point dimension, 1..3 (ignored for CKINV_DENSE) */
+  int32_t d;               /* sketch width r of Sec. 3, 16 <= d <= 512, d % 16 == 0 */
+  int32_t block_rows;      /* TSQR leaf height b (>= d); 0 = automatic */
+  int32_t prec;            /* ckinv_precision of the sketch contraction */
+  uint64_t seed;           /* seed of the counter-based generator drawing R and P */
+  int32_t refine_steps;    /* FP64 iterative-refinement steps of the final solve (0..4) */
+  int32_t tree_fp64_levels;/* top levels of the R tree combined in FP64; -1 = all */
+  int32_t leaf_fp64;       /* 1: per-block Householder (and so the whole tree) in FP64 */
+  int32_t reserved;        /* must be 0 */
+} ckinv_plan_desc;
+
+typedef struct ckinv_ctx ckinv_ctx;       /* workspaces, cached Omega, error string */
+typedef struct ckinv_factor ckinv_factor; /* R, Q_hat, LU(B), LU(C'), reflectors */
+
+/* Library version string (static storage). */
+const char *ckinv_version(void);
+
+/* Number of CUDA kernel launches the library has issued since it was loaded (all
+ * contexts and threads); a diagnostic for counting the work of a call. */
+unsigned long long ckinv_kernel_launches(void);
+
+/* Create a context on CUDA device `device` (must be sm_103).  *ctx receives the
+ * handle; on failure *ctx is NULL and the status says why. */
+ckinv_status ckinv_create(ckinv_ctx **ctx, int device);
+
+/* Synchronise the context's device and free everything it owns.  NULL is allowed. */
+ckinv_status ckinv_destroy(ckinv_ctx *ctx);
+
+/* One-line description of the last error on this context (static if ctx is NULL). */
+const char *ckinv_last_error(const ckinv_ctx *ctx);
+
+/* Synchronise `stream` and report device-detected failures of earlier asynchronous
+ * calls on this context (bounded-wait timeout, zero LU pivot, list overflow) as a
+ * status; clears the device error word. */
+ckinv_status ckinv_check(ckinv_ctx *ctx, ckinv_stream stream);
+
+/* Omega of Definition 1 (Sec. 3.2) as drawn from `seed`:
+ *   sign_bits: ceil(n/32) uint32 words; bit (k % 32) of word k/32 is 1 iff r_k = -1;
+ *   cols:      d int32 column indices p_0 < ... < p_{d-1} in [0, N).
+ * Both device, caller-owned.  Pass NULL for an output that is not wanted. */
+ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed,
+                         uint32_t *sign_bits, int32_t *cols, ckinv_stream stream);
+
+/* Sketch Y = K0 Omega (Sec. 3.1-3.2; Sec. 3.3's K_hat), computed matrix-free from the
+ * points: kernel tiles are evaluated on the fly and contracted with Omega.
+ *   points: n x dim FP32 row-major (x_i at points[i*dim]); NULL for CKINV_DENSE.
+ *   K, ldk: n x n FP32 column-major kernel matrix for CKINV_DENSE (ldk >= n), else NULL.
+ *   Y, ldy: n x d FP32 column-major output (ldy >= n).
+ * No nugget enters the sketch.  plan->prec selects the contraction precision. */
+ckinv_status ckinv_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                          const ckinv_kernel *kern, const float *points,
+                          const float *K, int64_t ldk, float *Y, int64_t ldy,
+                          ckinv_stream stream);
+
+/* Derivative sketch dK0/dlog(l) Omega (same layout as ckinv_sketch); used by the
+ * gradient.  Not defined for CKINV_DENSE. */
+ckinv_status ckinv_sketch_dlogl(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                                const ckinv_kernel *kern, const float *points,
+                                float *Yd, int64_t ldy, ckinv_stream stream);
+
+/* Blocked TSQR of Y (Sec. 3.3, Eqs. 1-4) and the low-rank core B = Omega^T Q_hat,
+ * C' = R^T + tau B with their LU factorisations (FP64).  Y is overwritten by the leaf
+ * Householder vectors.  *out receives a library-owned factor (free with
+ * ckinv_factor_free) holding Q_hat (n x d FP32) and six d x d FP64 matrices; it records
+ * plan->refine_steps for ckinv_solve.  The factor is usable once `stream` reaches this
+ * point.  A zero pivot in LU(B) or LU(C') is reported by the next ckinv_check. */
+ckinv_status ckinv_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                        const ckinv_kernel *kern, float *Y, int64_t ldy,
+                        ckinv_factor **out, ckinv_stream stream);
+
+/* Free a factor without host synchronisation: its memory is released in the order of the
+ * stream it was created on, so work on other streams that reads it must be complete (or
+ * ordered before that stream's current point).  NULL is allowed. */
+ckinv_status ckinv_factor_free(ckinv_factor *f);
+
+/* Copy the factor's R (d x d FP64, column-major, ld = d, diag(R) >= 0) to device R. */
+ckinv_status ckinv_factor_r(const ckinv_factor *f, double *R, ckinv_stream stream);
+
+/* Copy the explicit Q_hat (n x d FP32) to device Q (column-major, ldq >= n). */
+ckinv_status ckinv_factor_q(const ckinv_factor *f, float *Q, int64_t ldq,
+                            ckinv_stream stream);
+
+/* Copy B = Omega^T Q_hat and C' = R^T + tau B (d x d FP64, ld = d) to device buffers
+ * (either may be NULL) and write log det K_tilde = (n-d) ln tau + ln|det C'| -
+ * ln|det B| to host *logdet (synchronises `stream`; may be NULL). */
+ckinv_status ckinv_factor_core(const ckinv_factor *f, double *B, double *Cp,
+                               double *logdet, ckinv_stream stream);
+
+/* X = K_tilde^-1 A (Sec. 1's R^-1 Q^T A in Woodbury form), then plan->refine_steps
+ * steps of FP64 iterative refinement X += K_tilde^-1 (A - K_tilde X).
+ *   A: n x m FP32 (lda >= n);  X: n x m FP32 (ldx >= n); X may equal A.  1 <= m <= 256. */
+ckinv_status ckinv_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A,
+                         int64_t lda, int32_t m, float *X, int64_t ldx,
+                         ckinv_stream stream);
+
+/* One call for the whole path: sketch, TSQR, core and solve.  points, A and X may be
+ * host or device pointers (host buffers are staged through device memory inside the
+ * call, which then synchronises `stream`). */
+ckinv_status ckinv_kinv_a(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                          const ckinv_kernel *kern, const float *points,
+                          const float *A, int64_t lda, int32_t m, float *X,
+                          int64_t ldx, ckinv_stream stream);
+
+/* Gaussian negative log-likelihood of targets y (n FP32, device) under K_tilde,
+ *   NLL = 1/2 y^T K_tilde^-1 y + 1/2 log det K_tilde + n/2 ln(2 pi),
+ * and its gradient with respect to (log l, log variance, log nugget), written to
+ * host *nll and host grad[3] after synchronising `stream`. */
+ckinv_status ckinv_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                            const ckinv_kernel *kern, const float *points,
+                            const float *y, double *nll, double *grad,
+                            ckinv_stream stream);
+
+/* Batched form over nprob independent problems (uneven n): plans[p], kerns[p],
+ * points[p], y[p] as above (device pointers in HOST arrays); nll[p] and
+ * grad[3p..3p+2] are host outputs.  The per-stage kernels of all problems run as one
+ * launch each, and the whole sequence is replayed as one CUDA graph. */
+ckinv_status ckinv_nll_grad_batched(ckinv_ctx *ctx, int32_t nprob,
+                                    const ckinv_plan_desc *plans,
+                                    const ckinv_kernel *kerns,
+                                    const float *const *points, const float *const *y,
+                                    double *nll, double *grad, ckinv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CKINV_H */

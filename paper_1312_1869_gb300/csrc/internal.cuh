@@ -1,0 +1,224 @@
+// Internal declarations of the ckinv CUDA library (sm_103a).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/ckinv.h"
+
+namespace ckinv {
+
+// ----------------------------------------------------------------------------- errors
+struct Error {
+  ckinv_status st;
+  std::string msg;
+};
+
+#define CK_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      return ::ckinv::Error{e_ == cudaErrorMemoryAllocation ? CKINV_ENOMEM         \
+                                                            : CKINV_ECUDA,          \
+                            std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+    }                                                                              \
+  } while (0)
+
+#define CK_TRY(expr)                                                               \
+  do {                                                                             \
+    ::ckinv::Error er_ = (expr);                                                   \
+    if (er_.st != CKINV_OK) return er_;                                            \
+  } while (0)
+
+inline Error ok() { return Error{CKINV_OK, std::string()}; }
+
+// Host-side count of kernel launches issued by the library (diagnostics).
+unsigned long long &launch_counter();
+inline void note_launch() { __atomic_add_fetch(&launch_counter(), 1ull, __ATOMIC_RELAXED); }
+inline Error fail(ckinv_status s, const std::string &m) { return Error{s, m}; }
+
+// Device error word bits (ctx->d_err); the host maps them to a status.
+enum : int {
+  DERR_TIMEOUT = 1,      // a bounded mbarrier / flag wait ran out
+  DERR_SINGULAR = 2,     // zero pivot in an LU
+  DERR_CAPACITY = 4,     // an on-device list overflowed its buffer
+};
+
+// ----------------------------------------------------------------------------- context
+struct OmegaCache {
+  int64_t n = -1;
+  int32_t d = -1;
+  uint64_t seed = 0;
+  uint32_t *bits = nullptr;     // ceil(n/32) words
+  int32_t *cols = nullptr;      // d
+  __nv_bfloat16 *omegaT = nullptr;  // d x kpad, row j = Omega column j (unscaled +-1)
+  int64_t kpad = 0;
+  size_t omegaT_bytes = 0;
+};
+
+}  // namespace ckinv
+
+struct ckinv_ctx {
+  // pinned host staging ring for small descriptor uploads (no host synchronisation)
+  struct Stage {
+    void *host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+  } stage[8];
+  int stage_next = 0;
+  int device = 0;
+  int sm_count = 0;
+  std::string err;
+  ckinv::OmegaCache om;
+  int *d_err = nullptr;               // device error word
+  // scratch of the Omega draw
+  uint32_t *hist = nullptr;           // 65536 bins
+  unsigned long long *cand = nullptr; // candidate (key) list
+  uint32_t *cand_idx = nullptr;
+  uint32_t *small = nullptr;          // small counters
+  size_t cand_cap = 0;
+};
+
+struct ckinv_factor {
+  ckinv_ctx *ctx = nullptr;
+  int device = 0;
+  cudaStream_t stream = nullptr;   // creation stream: memory is released in its order
+  int64_t n = 0;
+  int32_t d = 0;
+  double tau = 0;
+  float *Q = nullptr;        // n x d explicit Q_hat (ld = n)
+  double *R = nullptr;       // d x d, diag >= 0
+  double *B = nullptr;       // d x d  Omega^T Q_hat
+  double *Cp = nullptr;      // d x d  R^T + tau B
+  double *luB = nullptr;     // packed LU of B
+  double *luC = nullptr;     // packed LU of C'
+  int32_t *pivB = nullptr;
+  int32_t *pivC = nullptr;
+  double *logdet_parts = nullptr;  // [ln|det B|, ln|det C'|]
+  uint32_t *bits = nullptr;  // Omega signs (copy)
+  int32_t *cols = nullptr;   // Omega columns (copy)
+  double omega_scale = 0;
+  int refine_steps = 0;
+};
+
+namespace ckinv {
+
+// ----------------------------------------------------------------------------- helpers
+inline int64_t padded_order(int64_t n) {
+  int64_t N = 1;
+  while (N < n) N <<= 1;
+  return N;
+}
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Kernel parameters as the device code consumes them.
+struct KernelParams {
+  int kind;          // CKINV_SE / CKINV_MATERN52
+  float inv_l;       // 1/l
+  float c_se;        // log2(e) / (2 l^2): SE value = exp2(-r^2 c_se)
+  float coord_scale; // sqrt(c_se) for SE (points pre-scaled), 1 for Matern
+  double scale;      // variance * omega scale c, applied in the epilogue
+  double ell;        // lengthscale (FP64 evaluation of the FP32 form)
+  double var;        // variance
+};
+
+// Upload `bytes` of host data to device memory `dst` on `st` through the pinned staging
+// ring: the host does not wait for the stream unless the ring slot is still in flight.
+Error stage_upload(ckinv_ctx *ctx, const void *src, size_t bytes, void *dst, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- Omega
+Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream_t st);
+Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st);   // ctx->om.omegaT
+
+// ----------------------------------------------------------------------------- sketch
+Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp,
+                  const float *points, const float *K, int64_t ldk, bool deriv,
+                  float *Y, int64_t ldy, cudaStream_t st);
+Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
+                const KernelParams &kp, const float *points, bool deriv, float *Y,
+                int64_t ldy, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- TSQR
+struct TsqrOut {
+  float *Q;     // n x d (ld n), explicit, column signs folded in
+  double *R;    // d x d, diag >= 0
+};
+Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64,
+                  float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
+int auto_block_rows(int64_t n, int d, int sm_count);
+
+// ----------------------------------------------------------------------------- low rank
+// G (d1 x d2, FP64, ld d1) = L^T M over n rows.  L = explicit FP32 (ldl) or, when
+// L == nullptr, Omega generated from bits/cols/scale.
+Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl,
+             const uint32_t *bits, const int32_t *cols, double oscale, const float *M,
+             int64_t ldm, double *G, cudaStream_t st);
+Error lu_factor_f64(ckinv_ctx *ctx, int n, double *A, int32_t *piv, double *logabsdet,
+                    cudaStream_t st);
+Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda,
+                    int m, float *X, int64_t ldx, int refine_steps, cudaStream_t st);
+Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st);
+// X (d x m FP64) <- op(A)^-1 X for a packed LU with LAPACK interchanges.
+Error lu_solve_dev(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st);
+// C (d x m) = op(A) Bm, FP64, ld = d.
+Error gemm_small_dev(int d, int m, const double *A, const double *Bm, double *C, int transA, cudaStream_t st);
+
+}  // namespace ckinv
+
+// ----------------------------------------------------------------------------- device
+#ifdef __CUDACC__
+namespace ckinv {
+namespace dev {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                               uint32_t c3, uint32_t k0, uint32_t k1) {
+  // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 S-box, key bumped by
+  // the Weyl constants between rounds.
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Unit-variance kernel value (or its d/dlog(l)) from the squared distance r2 computed
+// in pre-scaled coordinates (SE: coordinates scaled by sqrt(c_se), so r2s = r^2 c_se;
+// Matern: unscaled, r2s = r^2).
+__device__ __forceinline__ float kernel_value(int kind, float r2s, float inv_l, bool deriv) {
+  if (kind == CKINV_SE) {
+    float v = ex2_approx(-r2s);
+    // d/dlog l of exp(-r^2/(2l^2)) = exp(.) * r^2/l^2 = exp(.) * r2s * 2 ln2
+    return deriv ? v * (r2s * 1.3862943611198906f) : v;
+  } else {
+    float r = sqrtf(r2s);
+    float u = 2.2360679774997896f * r * inv_l;
+    float e = ex2_approx(-u * 1.4426950408889634f);
+    return deriv ? (u * u * (1.0f / 3.0f)) * (1.0f + u) * e
+                 : (1.0f + u + u * u * (1.0f / 3.0f)) * e;
+  }
+}
+
+}  // namespace dev
+}  // namespace ckinv
+#endif

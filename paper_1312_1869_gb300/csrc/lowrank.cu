@@ -1,0 +1,509 @@
+// Low-rank core and solve (Sec. 1: K^-1 A = R^-1 Q^T A; proof of Theorem 3:
+// P_Khat K = R^-1 Q^T K), completed with a nugget in Woodbury form:
+//   B = Omega^T Q_hat,  C' = R^T + tau B,
+//   K_tilde^-1 A = tau^-1 (A - Q_hat C'^-1 R^T Q_hat^T A),
+//   K_tilde X = tau X + Q_hat B^-1 R^T Q_hat^T X    (refinement residual, FP64).
+// Long contractions over the n rows run on the CUDA cores in FP32 with FP64 accumulation
+// across 256-row chunks; every d x d operation (LU, triangular solves) is FP64.
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ckinv {
+namespace {
+
+// ---------------------------------------------------------------- G = L^T M over n rows
+// Tile 64 x 64 of G per CTA, rows split over gridDim.z chunks; FP32 FMA inside 256-row
+// sub-chunks, FP64 accumulation across them, FP64 atomics into G (zeroed by the caller).
+template <bool OMEGA>
+__global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const float *__restrict__ L,
+                                                int64_t ldl, const uint32_t *__restrict__ bits,
+                                                const int32_t *__restrict__ cols, double oscale,
+                                                const float *__restrict__ M, int64_t ldm, double *G,
+                                                int64_t rows_per_split) {
+  __shared__ float Ls[32][64 + 4];
+  __shared__ float Ms[32][64 + 4];
+  __shared__ uint32_t pc[64];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  const int64_t rb = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t re = min(n, rb + rows_per_split);
+  if (OMEGA)
+    for (int c = tid; c < 64; c += 256) pc[c] = (i0 + c < d1) ? (uint32_t)cols[i0 + c] : 0u;
+  float acc[4][4];
+  double accd[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = 0.f; accd[a][b] = 0.0; }
+  __syncthreads();
+  int step = 0;
+  for (int64_t k0 = rb; k0 < re; k0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int e = tid + 256 * q;
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      float lv = 0.f, mv = 0.f;
+      if (k < re) {
+        if (i0 + c < d1) {
+          if (OMEGA) {
+            uint32_t s = (bits[k >> 5] >> (k & 31)) & 1u;
+            s ^= (uint32_t)(__popcll((unsigned long long)k & (unsigned long long)pc[c]) & 1);
+            lv = s ? -1.0f : 1.0f;
+          } else {
+            lv = L[k + (int64_t)(i0 + c) * ldl];
+          }
+        }
+        if (j0 + c < d2) mv = M[k + (int64_t)(j0 + c) * ldm];
+      }
+      Ls[kk][c] = lv;
+      Ms[kk][c] = mv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { a[t] = Ls[kk][ty * 4 + t]; b[t] = Ms[kk][tx * 4 + t]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+    if (++step == 8) {
+      step = 0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) { accd[x][y] += (double)acc[x][y]; acc[x][y] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      int i = i0 + ty * 4 + x, j = j0 + tx * 4 + y;
+      if (i < d1 && j < d2)
+        atomicAdd(&G[i + (int64_t)j * d1], (OMEGA ? oscale : 1.0) * (accd[x][y] + (double)acc[x][y]));
+    }
+}
+
+// G = Q^T X with FP64 arithmetic (Q FP32 n x d, X FP32 n x m): the products of two FP32
+// numbers are exact in FP64, so this is the residual-grade contraction of the refinement.
+__global__ void __launch_bounds__(256) k_tsprod_f64(int64_t n, int d1, int d2, const float *__restrict__ L,
+                                                    int64_t ldl, const float *__restrict__ M, int64_t ldm,
+                                                    double *G, int64_t rows_per_split) {
+  __shared__ float Ls[32][64 + 4];
+  __shared__ float Ms[32][32 + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // 64 x 32 tile: 4 x 2 per thread
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
+  const int64_t rb = (int64_t)blockIdx.z * rows_per_split;
+  const int64_t re = min(n, rb + rows_per_split);
+  double acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) { acc[a][0] = 0.0; acc[a][1] = 0.0; }
+  for (int64_t k0 = rb; k0 < re; k0 += 32) {
+    for (int e = tid; e < 32 * 64; e += 256) {
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      Ls[kk][c] = (k < re && i0 + c < d1) ? L[k + (int64_t)(i0 + c) * ldl] : 0.f;
+    }
+    for (int e = tid; e < 32 * 32; e += 256) {
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      Ms[kk][c] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 32; ++kk) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        double a = (double)Ls[kk][ty * 4 + x];
+        acc[x][0] = fma(a, (double)Ms[kk][tx * 2], acc[x][0]);
+        acc[x][1] = fma(a, (double)Ms[kk][tx * 2 + 1], acc[x][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      int i = i0 + ty * 4 + x, j = j0 + tx * 2 + y;
+      if (i < d1 && j < d2) atomicAdd(&G[i + (int64_t)j * d1], acc[x][y]);
+    }
+}
+
+// ---------------------------------------------------------------- LU (FP64, cooperative)
+// Right-looking LU with partial pivoting of nmat d x d column-major matrices (ld = d),
+// LAPACK-style interchanges piv[j].  Block `m` (< nmat) runs the pivot step of matrix m;
+// all blocks share the rank-1 updates.  logabs[m] = sum log|U_jj|.
+__global__ void k_lu_coop(int nmat, int d, double *const *mats, int32_t *const *pivs, double *logabs,
+                          int *err) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  __shared__ double s_logabs;
+  if (threadIdx.x == 0) s_logabs = 0.0;
+  for (int j = 0; j < d; ++j) {
+    if ((int)blockIdx.x < nmat) {
+      double *A = mats[blockIdx.x];
+      // pivot search
+      double best = -1.0;
+      int bi = j;
+      for (int i = j + threadIdx.x; i < d; i += blockDim.x) {
+        double v = fabs(A[i + (int64_t)j * d]);
+        if (v > best) { best = v; bi = i; }
+      }
+      sval[threadIdx.x] = best;
+      sidx[threadIdx.x] = bi;
+      __syncthreads();
+      for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+          double o = sval[threadIdx.x + off];
+          int oi = sidx[threadIdx.x + off];
+          if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+            sval[threadIdx.x] = o;
+            sidx[threadIdx.x] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      const int p = sidx[0];
+      if (p != j)
+        for (int c = threadIdx.x; c < d; c += blockDim.x) {
+          double t = A[j + (int64_t)c * d];
+          A[j + (int64_t)c * d] = A[p + (int64_t)c * d];
+          A[p + (int64_t)c * d] = t;
+        }
+      __syncthreads();
+      const double piv = A[j + (int64_t)j * d];
+      if (threadIdx.x == 0) {
+        pivs[blockIdx.x][j] = p;
+        if (piv == 0.0) atomicOr(err, DERR_SINGULAR);
+        else s_logabs += log(fabs(piv));
+      }
+      const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
+      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) A[i + (int64_t)j * d] *= inv;
+      __threadfence();
+    }
+    grid.sync();
+    // rank-1 update of the trailing block of every matrix
+    const int64_t t = d - j - 1;
+    const int64_t per = t * t;
+    const int64_t total = per * nmat;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int m = (int)(e / per);
+      int64_t w = e % per;
+      int i = j + 1 + (int)(w % t), c = j + 1 + (int)(w / t);
+      double *A = mats[m];
+      A[i + (int64_t)c * d] -= A[i + (int64_t)j * d] * A[j + (int64_t)c * d];
+    }
+    __threadfence();
+    grid.sync();
+  }
+  if ((int)blockIdx.x < nmat && threadIdx.x == 0) logabs[blockIdx.x] = s_logabs;
+}
+
+// ---------------------------------------------------------------- triangular solves
+// X (d x m, ld d) <- op(A)^-1 X with A = P L U packed (LAPACK interchanges).  One CTA per
+// right-hand side; column-oriented substitution (no reductions).
+__global__ void k_lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans) {
+  extern __shared__ double xs[];
+  const int c = blockIdx.x;
+  if (c >= m) return;
+  double *x = X + (int64_t)c * d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) xs[i] = x[i];
+  __syncthreads();
+  if (!trans) {
+    if (threadIdx.x == 0)
+      for (int j = 0; j < d; ++j) {
+        int p = piv[j];
+        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+      }
+    __syncthreads();
+    for (int j = 0; j < d; ++j) {          // L y = P x  (unit lower)
+      double xj = xs[j];
+      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) xs[i] -= LU[i + (int64_t)j * d] * xj;
+      __syncthreads();
+    }
+    for (int j = d - 1; j >= 0; --j) {     // U x = y
+      if (threadIdx.x == 0) xs[j] /= LU[j + (int64_t)j * d];
+      __syncthreads();
+      double xj = xs[j];
+      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= LU[i + (int64_t)j * d] * xj;
+      __syncthreads();
+    }
+  } else {
+    // A^T = U^T L^T P:  U^T z = x (lower), L^T w = z (unit upper), x = P^T w
+    for (int j = 0; j < d; ++j) {
+      if (threadIdx.x == 0) xs[j] /= LU[j + (int64_t)j * d];
+      __syncthreads();
+      double xj = xs[j];
+      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) xs[i] -= LU[j + (int64_t)i * d] * xj;
+      __syncthreads();
+    }
+    for (int j = d - 1; j >= 0; --j) {
+      double xj = xs[j];
+      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= LU[j + (int64_t)i * d] * xj;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int j = d - 1; j >= 0; --j) {
+        int p = piv[j];
+        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+      }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < d; i += blockDim.x) x[i] = xs[i];
+}
+
+// C (d x m) = op(A) (d x d) * Bm (d x m), FP64, ld = d.  transA: C = A^T B.
+__global__ void k_gemm_small(int d, int m, const double *A, const double *Bm, double *C, int transA,
+                             double alpha) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = blockIdx.y;
+  if (i >= d) return;
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double a = transA ? A[k + (int64_t)i * d] : A[i + (int64_t)k * d];
+    s = fma(a, Bm[k + (int64_t)c * d], s);
+  }
+  C[i + (int64_t)c * d] = alpha * s;
+}
+
+// C' = R^T + tau B  (and copies for the LUs)
+__global__ void k_make_core(int d, const double *R, const double *B, double tau, double *Cp, double *luB,
+                            double *luC) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += gridDim.x * blockDim.x) {
+    int i = e % d, j = e / d;
+    double c = R[j + (int64_t)i * d] + tau * B[e];
+    Cp[e] = c;
+    luC[e] = c;
+    luB[e] = B[e];
+  }
+}
+
+// X = (A - Q V) * inv_tau  (FP32 GEMM n x d x m; V is FP64 d x m, converted per tile).
+__global__ void __launch_bounds__(256) k_apply_x(int64_t n, int d, int m, const float *__restrict__ Q,
+                                                 int64_t ldq, const double *__restrict__ V,
+                                                 const float *__restrict__ A, int64_t lda, float *X,
+                                                 int64_t ldx, float inv_tau) {
+  __shared__ float Vs[64][33];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+  const int c0 = blockIdx.y * 32;
+  const int mc = min(32, m - c0);
+  float acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+  for (int k0 = 0; k0 < d; k0 += 64) {
+    __syncthreads();
+    for (int e = tid; e < 64 * 32; e += 256) {
+      int kk = e % 64, c = e / 64;
+      Vs[kk][c] = (k0 + kk < d && c < mc) ? (float)V[(k0 + kk) + (int64_t)(c0 + c) * d] : 0.f;
+    }
+    __syncthreads();
+    if (i < n) {
+      int kmax = min(64, d - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        float q = Q[i + (int64_t)(k0 + kk) * ldq];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fmaf(q, Vs[kk][c], acc[c]);
+      }
+    }
+  }
+  if (i < n)
+    for (int c = 0; c < mc; ++c)
+      X[i + (int64_t)(c0 + c) * ldx] = (A[i + (int64_t)(c0 + c) * lda] - acc[c]) * inv_tau;
+}
+
+// r = A - tau X - Q S  in FP64 (Q FP32, S FP64 d x m); r written as FP32 pair? no: FP32
+// is enough for the right-hand side of the correction solve once the cancellation has
+// happened in FP64.
+__global__ void __launch_bounds__(256) k_residual(int64_t n, int d, int m, const float *__restrict__ Q,
+                                                  int64_t ldq, const double *__restrict__ S,
+                                                  const float *__restrict__ A, int64_t lda,
+                                                  const float *__restrict__ X, int64_t ldx, double tau,
+                                                  float *Rs, int64_t ldr) {
+  __shared__ double Ss[64][33];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+  const int c0 = blockIdx.y * 32;
+  const int mc = min(32, m - c0);
+  double acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+  for (int k0 = 0; k0 < d; k0 += 64) {
+    __syncthreads();
+    for (int e = tid; e < 64 * 32; e += 256) {
+      int kk = e % 64, c = e / 64;
+      Ss[kk][c] = (k0 + kk < d && c < mc) ? S[(k0 + kk) + (int64_t)(c0 + c) * d] : 0.0;
+    }
+    __syncthreads();
+    if (i < n) {
+      int kmax = min(64, d - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        double q = (double)Q[i + (int64_t)(k0 + kk) * ldq];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fma(q, Ss[kk][c], acc[c]);
+      }
+    }
+  }
+  if (i < n)
+    for (int c = 0; c < mc; ++c) {
+      double a = (double)A[i + (int64_t)(c0 + c) * lda];
+      double x = (double)X[i + (int64_t)(c0 + c) * ldx];
+      Rs[i + (int64_t)(c0 + c) * ldr] = (float)(a - tau * x - acc[c]);
+    }
+}
+
+__global__ void k_add_inplace(int64_t n, int m, float *X, int64_t ldx, const float *D, int64_t ldd) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n, c = e / n;
+    X[i + c * ldx] += D[i + c * ldd];
+  }
+}
+
+int splits_for(const ckinv_ctx *ctx, int64_t n, int tiles) {
+  int want = std::max(1, (ctx->sm_count * 3) / std::max(1, tiles));
+  int64_t max_split = ceil_div(n, 256);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, max_split));
+}
+
+}  // namespace
+
+Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const uint32_t *bits,
+             const int32_t *cols, double oscale, const float *M, int64_t ldm, double *G, cudaStream_t st) {
+  CK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)d1 * d2, st));
+  int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 64);
+  int sp = splits_for(ctx, n, tx * ty);
+  int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
+  sp = (int)ceil_div(n, rps);
+  dim3 grid(tx, ty, sp);
+  if (L) ::ckinv::note_launch(), k_tsprod<false><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, G, rps);
+  else ::ckinv::note_launch(), k_tsprod<true><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, G, rps);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
+static Error tsprod_f64(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const float *M,
+                        int64_t ldm, double *G, cudaStream_t st) {
+  CK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)d1 * d2, st));
+  int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 32);
+  int sp = splits_for(ctx, n, tx * ty);
+  int64_t rps = ceil_div(ceil_div(n, sp), 32) * 32;
+  sp = (int)ceil_div(n, rps);
+  dim3 grid(tx, ty, sp);
+  ::ckinv::note_launch(), k_tsprod_f64<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, G, rps);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
+static Error lu_batch(ckinv_ctx *ctx, int nmat, int d, double **mats_h, int32_t **pivs_h, double *logabs,
+                      cudaStream_t st) {
+  double **mats = nullptr;
+  int32_t **pivs = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&mats, sizeof(double *) * nmat, st));
+  CK_CUDA(cudaMallocAsync((void **)&pivs, sizeof(int32_t *) * nmat, st));
+  CK_TRY(stage_upload(ctx, mats_h, sizeof(double *) * nmat, mats, st));
+  CK_TRY(stage_upload(ctx, pivs_h, sizeof(int32_t *) * nmat, pivs, st));
+  int per_sm = 0;
+  CK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_coop, 256, 0));
+  int grid = std::max(nmat, std::min(ctx->sm_count * std::max(per_sm, 1), ctx->sm_count));
+  int *err = ctx->d_err;
+  void *args[] = {(void *)&nmat, (void *)&d, (void *)&mats, (void *)&pivs, (void *)&logabs, (void *)&err};
+  note_launch();
+  CK_CUDA(cudaLaunchCooperativeKernel((void *)k_lu_coop, grid, 256, args, 0, st));
+  CK_CUDA(cudaFreeAsync(mats, st));
+  CK_CUDA(cudaFreeAsync(pivs, st));
+  return ok();
+}
+
+static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
+  ::ckinv::note_launch(), k_lu_solve<<<m, 256, sizeof(double) * d, st>>>(d, m, LU, piv, X, trans);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
+Error lu_solve_dev(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
+  return lu_solve(d, m, LU, piv, X, trans, st);
+}
+
+Error gemm_small_dev(int d, int m, const double *A, const double *Bm, double *C, int transA, cudaStream_t st) {
+  dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
+  ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, A, Bm, C, transA, 1.0);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
+Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
+  const int d = f->d;
+  CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
+  ::ckinv::note_launch(), k_make_core<<<64, 256, 0, st>>>(d, f->R, f->B, f->tau, f->Cp, f->luB, f->luC);
+  CK_CUDA(cudaGetLastError());
+  double *mats[2] = {f->luB, f->luC};
+  int32_t *pivs[2] = {f->pivB, f->pivC};
+  CK_TRY(lu_batch(ctx, 2, d, mats, pivs, f->logdet_parts, st));
+  return ok();
+}
+
+// X = K_tilde^-1 A, then refine_steps steps of refinement.
+Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda, int m, float *X,
+                    int64_t ldx, int refine_steps, cudaStream_t st) {
+  const int d = f->d;
+  const int64_t n = f->n;
+  double *Z = nullptr, *W = nullptr;
+  float *Acopy = nullptr, *Rs = nullptr, *Dx = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&Z, sizeof(double) * d * m, st));
+  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(double) * d * m, st));
+  const float *Ain = A;
+  if (refine_steps > 0 || X == A) {
+    // keep A: X may alias it and the refinement needs it
+    CK_CUDA(cudaMallocAsync((void **)&Acopy, sizeof(float) * n * m, st));
+    CK_CUDA(cudaMemcpy2DAsync(Acopy, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
+                              cudaMemcpyDeviceToDevice, st));
+    Ain = Acopy;
+    lda = n;
+  }
+  auto solve_into = [&](const float *rhs, int64_t ldr, float *out, int64_t ldo) -> Error {
+    CK_TRY(tsprod(ctx, n, d, m, f->Q, n, nullptr, nullptr, 0.0, rhs, ldr, Z, st));     // Z = Q^T rhs
+    dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
+    ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);                           // W = R^T Z
+    CK_CUDA(cudaGetLastError());
+    CK_TRY(lu_solve(d, m, f->luC, f->pivC, W, 0, st));                                   // W = C'^-1 W
+    dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 32));
+    ::ckinv::note_launch(), k_apply_x<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, rhs, ldr, out, ldo, (float)(1.0 / f->tau));
+    CK_CUDA(cudaGetLastError());
+    return ok();
+  };
+  CK_TRY(solve_into(Ain, lda, X, ldx));
+  if (refine_steps > 0) {
+    CK_CUDA(cudaMallocAsync((void **)&Rs, sizeof(float) * n * m, st));
+    CK_CUDA(cudaMallocAsync((void **)&Dx, sizeof(float) * n * m, st));
+    for (int s = 0; s < refine_steps; ++s) {
+      // S = B^-1 R^T Q^T X  (FP64)
+      CK_TRY(tsprod_f64(ctx, n, d, m, f->Q, n, X, ldx, Z, st));
+      dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
+      ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);
+      CK_CUDA(cudaGetLastError());
+      CK_TRY(lu_solve(d, m, f->luB, f->pivB, W, 0, st));
+      dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 32));
+      ::ckinv::note_launch(), k_residual<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, Ain, lda, X, ldx, f->tau, Rs, n);
+      CK_CUDA(cudaGetLastError());
+      CK_TRY(solve_into(Rs, n, Dx, n));
+      ::ckinv::note_launch(), k_add_inplace<<<(unsigned)std::min<int64_t>(ceil_div(n * m, 256), 65535), 256, 0, st>>>(n, m, X, ldx, Dx, n);
+      CK_CUDA(cudaGetLastError());
+    }
+  }
+  for (void *p : {(void *)Z, (void *)W, (void *)Acopy, (void *)Rs, (void *)Dx})
+    if (p) CK_CUDA(cudaFreeAsync(p, st));
+  return ok();
+}
+
+}  // namespace ckinv

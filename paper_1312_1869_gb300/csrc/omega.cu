@@ -1,0 +1,221 @@
+// Structured random matrix Omega = c R H_N P of Definition 1 (Sec. 3.2): the Rademacher
+// diagonal R and the column subsample P drawn from a counter-based generator, and the
+// BF16 copy of the unscaled +-1 pattern that the tensor-core sketch streams by TMA.
+//
+// Draw (reading; the paper names no generator): Philox4x32-10 with key (seed_lo,
+// seed_hi) and counter (index_lo, index_hi, stream, 0).  r_k = -1 iff bit 0 of word 0 at
+// stream 0 is set.  P = the d candidates c < N with the smallest 64-bit keys
+// (word0 << 32 | word1) at stream 1, ties to the smaller c, sorted ascending.
+#include "internal.cuh"
+
+namespace ckinv {
+namespace {
+
+__global__ void k_signs(int64_t n, uint32_t k0, uint32_t k1, uint32_t *bits) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t bit = 0;
+  if (k < n) {
+    uint4 w = dev::philox4x32_10((uint32_t)k, (uint32_t)(k >> 32), 0u, 0u, k0, k1);
+    bit = w.x & 1u;
+  }
+  uint32_t word = __ballot_sync(0xffffffffu, bit);
+  if ((threadIdx.x & 31) == 0 && k < n) bits[k >> 5] = word;
+}
+
+__device__ __forceinline__ unsigned long long cand_key(int64_t c, uint32_t k0, uint32_t k1) {
+  uint4 w = dev::philox4x32_10((uint32_t)c, (uint32_t)(c >> 32), 1u, 0u, k0, k1);
+  return ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
+}
+
+// Histogram of the top 16 key bits over all N candidates.
+__global__ void k_key_hist(int64_t N, uint32_t k0, uint32_t k1, uint32_t *hist) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long key = cand_key(c, k0, k1);
+    atomicAdd(&hist[key >> 48], 1u);
+  }
+}
+
+// One block of 1024 threads: find the bin t holding the d-th smallest key.
+// small[0] = t, small[1] = number of candidates in bins <= t.
+__global__ void k_pick_bin(const uint32_t *hist, int d, uint32_t *small) {
+  __shared__ uint32_t part[1024];
+  int t = threadIdx.x;
+  uint32_t s = 0;
+  for (int i = 0; i < 64; ++i) s += hist[t * 64 + i];
+  part[t] = s;
+  __syncthreads();
+  // inclusive scan (Hillis-Steele)
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = (t >= off) ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t before = (t == 0) ? 0u : part[t - 1];
+  if (before < (uint32_t)d && part[t] >= (uint32_t)d) {
+    uint32_t cum = before;
+    for (int i = 0; i < 64; ++i) {
+      cum += hist[t * 64 + i];
+      if (cum >= (uint32_t)d) {
+        small[0] = (uint32_t)(t * 64 + i);
+        small[1] = cum;
+        break;
+      }
+    }
+  }
+}
+
+__global__ void k_collect(int64_t N, uint32_t k0, uint32_t k1, const uint32_t *small,
+                          unsigned long long *cand, uint32_t *cand_idx, uint32_t cap,
+                          uint32_t *counter) {
+  uint32_t tbin = small[0];
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long key = cand_key(c, k0, k1);
+    if ((uint32_t)(key >> 48) <= tbin) {
+      uint32_t pos = atomicAdd(counter, 1u);
+      if (pos < cap) {
+        cand[pos] = key;
+        cand_idx[pos] = (uint32_t)c;
+      }
+    }
+  }
+}
+
+// One block: sort the (key, index) candidates, keep the d smallest, sort their indices.
+constexpr int kSortCap = 4096;
+__global__ void k_finalize(const unsigned long long *cand, const uint32_t *cand_idx,
+                           const uint32_t *counter, int d, int32_t *cols, int *err) {
+  __shared__ unsigned long long skey[kSortCap];
+  __shared__ uint32_t sidx[kSortCap];
+  uint32_t cnt = *counter;
+  if (cnt > (uint32_t)kSortCap || cnt < (uint32_t)d) {
+    if (threadIdx.x == 0) atomicOr(err, DERR_CAPACITY);
+    return;
+  }
+  int P = 1;
+  while (P < (int)cnt) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    skey[i] = (i < (int)cnt) ? cand[i] : ~0ull;
+    sidx[i] = (i < (int)cnt) ? cand_idx[i] : 0xffffffffu;
+  }
+  __syncthreads();
+  // bitonic sort by (key, index)
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          bool up = ((i & k) == 0);
+          unsigned long long a = skey[i], b = skey[ixj];
+          uint32_t ia = sidx[i], ib = sidx[ixj];
+          bool gt = (a > b) || (a == b && ia > ib);
+          if (gt == up) {
+            skey[i] = b; skey[ixj] = a;
+            sidx[i] = ib; sidx[ixj] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // the first d entries are P; sort their indices ascending (reuse skey as index keys)
+  int Q = 1;
+  while (Q < d) Q <<= 1;
+  for (int i = threadIdx.x; i < Q; i += blockDim.x)
+    skey[i] = (i < d) ? (unsigned long long)sidx[i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= Q; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          bool up = ((i & k) == 0);
+          unsigned long long a = skey[i], b = skey[ixj];
+          if ((a > b) == up) { skey[i] = b; skey[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < d; i += blockDim.x) cols[i] = (int32_t)skey[i];
+}
+
+// omegaT[j * kpad + k] = bf16(+-1) = r_k (-1)^popc(k & p_j) for k < n, 0 for k >= n.
+__global__ void k_omegaT(int64_t n, int64_t kpad, int d, const uint32_t *bits,
+                         const int32_t *cols, __nv_bfloat16 *out) {
+  int j = blockIdx.y;
+  uint32_t p = (uint32_t)cols[j];
+  int64_t k2 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (k2 >= kpad) return;
+  float v[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    int64_t k = k2 + t;
+    if (k < n) {
+      uint32_t s = (bits[k >> 5] >> (k & 31)) & 1u;
+      s ^= (uint32_t)(__popcll((unsigned long long)k & (unsigned long long)p) & 1);
+      v[t] = s ? -1.0f : 1.0f;
+    } else {
+      v[t] = 0.0f;
+    }
+  }
+  __nv_bfloat162 pr = __floats2bfloat162_rn(v[0], v[1]);
+  *reinterpret_cast<__nv_bfloat162 *>(out + (int64_t)j * kpad + k2) = pr;
+}
+
+}  // namespace
+
+Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream_t st) {
+  OmegaCache &om = ctx->om;
+  if (om.n == n && om.d == d && om.seed == seed && om.bits) return ok();
+  int64_t N = padded_order(n);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (om.bits) { cudaFreeAsync(om.bits, st); om.bits = nullptr; }
+  if (om.cols) { cudaFreeAsync(om.cols, st); om.cols = nullptr; }
+  if (om.omegaT) { cudaFreeAsync(om.omegaT, st); om.omegaT = nullptr; om.omegaT_bytes = 0; }
+  om.n = -1;
+  CK_CUDA(cudaMallocAsync((void **)&om.bits, sizeof(uint32_t) * ceil_div(n, 32), st));
+  CK_CUDA(cudaMallocAsync((void **)&om.cols, sizeof(int32_t) * d, st));
+  if (!ctx->hist) {
+    CK_CUDA(cudaMalloc((void **)&ctx->hist, sizeof(uint32_t) * 65536));
+    CK_CUDA(cudaMalloc((void **)&ctx->small, sizeof(uint32_t) * 16));
+    ctx->cand_cap = kSortCap;
+    CK_CUDA(cudaMalloc((void **)&ctx->cand, sizeof(unsigned long long) * ctx->cand_cap));
+    CK_CUDA(cudaMalloc((void **)&ctx->cand_idx, sizeof(uint32_t) * ctx->cand_cap));
+  }
+  ::ckinv::note_launch(), k_signs<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, k0, k1, om.bits);
+  CK_CUDA(cudaMemsetAsync(ctx->hist, 0, sizeof(uint32_t) * 65536, st));
+  CK_CUDA(cudaMemsetAsync(ctx->small, 0, sizeof(uint32_t) * 16, st));
+  int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->sm_count * 8);
+  ::ckinv::note_launch(), k_key_hist<<<grid, 256, 0, st>>>(N, k0, k1, ctx->hist);
+  ::ckinv::note_launch(), k_pick_bin<<<1, 1024, 0, st>>>(ctx->hist, d, ctx->small);
+  ::ckinv::note_launch(), k_collect<<<grid, 256, 0, st>>>(N, k0, k1, ctx->small, ctx->cand, ctx->cand_idx,
+                                  (uint32_t)ctx->cand_cap, ctx->small + 2);
+  ::ckinv::note_launch(), k_finalize<<<1, 1024, 0, st>>>(ctx->cand, ctx->cand_idx, ctx->small + 2, d, om.cols,
+                                 ctx->d_err);
+  CK_CUDA(cudaGetLastError());
+  om.n = n;
+  om.d = d;
+  om.seed = seed;
+  return ok();
+}
+
+Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st) {
+  OmegaCache &om = ctx->om;
+  int64_t kpad = ceil_div(om.n, 64) * 64;
+  size_t bytes = sizeof(__nv_bfloat16) * (size_t)kpad * om.d;
+  if (om.omegaT && om.omegaT_bytes == bytes && om.kpad == kpad) return ok();
+  if (om.omegaT) cudaFreeAsync(om.omegaT, st);
+  om.omegaT = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&om.omegaT, bytes, st));
+  om.omegaT_bytes = bytes;
+  om.kpad = kpad;
+  dim3 grid((unsigned)ceil_div(kpad / 2, 256), (unsigned)om.d);
+  ::ckinv::note_launch(), k_omegaT<<<grid, 256, 0, st>>>(om.n, kpad, om.d, om.bits, om.cols, om.omegaT);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
+}  // namespace ckinv

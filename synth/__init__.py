@@ -26,7 +26,7 @@ MATERN52 = 1
 # The five workloads (sizes and hyper-parameters of each).
 CONFIGS = {
     "c1_plain_n2048": dict(n=2048, dim=2, kind=SE, ell=0.2, var=1.0, tau=1e-6, d=64,
-                           m=4, block_rows=512, seed=0),
+                           m=4, block_rows=512, seed=0, leaf_fp64=1),
     "c2_dense_n65536": dict(n=65536, dim=3, kind=MATERN52, ell=0.15, var=1.0, tau=1e-5,
                             d=256, m=16, block_rows=1024, seed=0),
     "c3_bf16_n262144": dict(n=262144, dim=2, kind=SE, ell=0.1, var=1.0, tau=1e-6, d=512,
