@@ -137,8 +137,8 @@ ckinv_status ckinv_sketch_dlogl(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
                                 float *Yd, int64_t ldy, ckinv_stream stream);
 
 /* Blocked TSQR of Y (Sec. 3.3, Eqs. 1-4) and the low-rank core B = Omega^T Q_hat,
- * C' = R^T + tau B with their LU factorisations (FP64).  Y is overwritten by the leaf
- * Householder vectors.  *out receives a library-owned factor (free with
+ * C' = R^T + tau B with their LU factorisations (FP64).  Y is read, not modified.
+ * *out receives a library-owned factor (free with
  * ckinv_factor_free) holding Q_hat (n x d FP32) and six d x d FP64 matrices; it records
  * plan->refine_steps for ckinv_solve.  The factor is usable once `stream` reaches this
  * point.  A zero pivot in LU(B) or LU(C') is reported by the next ckinv_check. */

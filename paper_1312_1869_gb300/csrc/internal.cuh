@@ -147,8 +147,15 @@ struct TsqrOut {
   double *R;    // d x d, diag >= 0
 };
 Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64,
-                  float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
+                  const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
 int auto_block_rows(int64_t n, int d, int sm_count);
+
+// ----------------------------------------------------------------------------- GEMM
+// C_b = alpha op(A_b) B_b + beta C_b for b < batch (column-major, strided batches).
+template <typename T>
+Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
+                   int64_t sA, const T *B, int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC,
+                   int batch, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- low rank
 // G (d1 x d2, FP64, ld d1) = L^T M over n rows.  L = explicit FP32 (ldl) or, when
