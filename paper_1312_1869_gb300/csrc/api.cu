@@ -118,8 +118,12 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
   }
   CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   KernelParams kp = make_params(plan, kern);
-  if (kern->kind == CKINV_DENSE)
+  if (kern->kind == CKINV_DENSE) {
+    // K is symmetric: its column i is read as row i (16-byte rows for the tensor-core path)
+    if (plan->prec != CKINV_FP32 && ldk % 4 == 0 && (reinterpret_cast<uintptr_t>(K) & 15) == 0)
+      return dense_tc(ctx, plan->n, plan->n, plan->d, plan->prec, K, ldk, kp.scale, Y, ldy, nullptr, 0, 0, st);
     return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, nullptr, K, ldk, false, Y, ldy, st);
+  }
   if (plan->prec == CKINV_FP32)
     return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, points, nullptr, 0, deriv, Y, ldy, st);
   return sketch_tc(ctx, plan->n, plan->dim, plan->d, plan->prec, kp, points, deriv, Y, ldy, st);
@@ -127,8 +131,8 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
 
 void factor_release(ckinv_factor *f) {
   if (!f) return;
-  for (void *p : {(void *)f->Q, (void *)f->R, (void *)f->B, (void *)f->Cp, (void *)f->luB, (void *)f->luC,
-                  (void *)f->pivB, (void *)f->pivC, (void *)f->logdet_parts, (void *)f->bits, (void *)f->cols})
+  for (void *p : {(void *)f->Q, (void *)f->R, (void *)f->B, (void *)f->Cp, (void *)f->luB, (void *)f->pivB,
+                  (void *)f->logdet_parts, (void *)f->bits, (void *)f->cols})
     if (p) cudaFreeAsync(p, f->stream);
   delete f;
 }
@@ -150,6 +154,7 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
   f->d = d;
   f->tau = kern->nugget;
   f->refine_steps = plan->refine_steps;
+  f->prec = plan->prec;
   f->omega_scale = 1.0 / std::sqrt((double)padded_order(n));
   Error e = ok();
   auto alloc = [&](void **p, size_t bytes) {
@@ -162,10 +167,12 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
   alloc((void **)&f->R, sizeof(double) * dd);
   alloc((void **)&f->B, sizeof(double) * dd);
   alloc((void **)&f->Cp, sizeof(double) * dd);
-  alloc((void **)&f->luB, sizeof(double) * dd);
-  alloc((void **)&f->luC, sizeof(double) * dd);
-  alloc((void **)&f->pivB, sizeof(int32_t) * d);
-  alloc((void **)&f->pivC, sizeof(int32_t) * d);
+  alloc((void **)&f->luB, sizeof(double) * dd * 2);     // luC = luB + d*d
+  alloc((void **)&f->pivB, sizeof(int32_t) * d * 2);     // pivC = pivB + d
+  if (e.st == CKINV_OK) {
+    f->luC = f->luB + dd;
+    f->pivC = f->pivB + d;
+  }
   alloc((void **)&f->logdet_parts, sizeof(double) * 2);
   alloc((void **)&f->bits, sizeof(uint32_t) * ceil_div(n, 32));
   alloc((void **)&f->cols, sizeof(int32_t) * d);
@@ -294,7 +301,13 @@ Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kerne
     if ((e = tsprod(ctx, n, d, 1, f->Q, n, nullptr, nullptr, 0, alpha, n, beta, st)).st) break;
     if ((e = tsprod(ctx, n, d, 1, Yd, n, nullptr, nullptr, 0, alpha, n, g3, st)).st) break;
     if ((e = tsprod(ctx, n, d, d, f->Q, n, nullptr, nullptr, 0, Yd, n, G1, st)).st) break;
-    if ((e = tsprod(ctx, n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, Yd, n, G2, st)).st) break;
+    if (n % 4 == 0 && plan->prec != CKINV_FP32) {
+      // G2 = Omega^T Yd on the tensor cores (rows of A are the columns of Yd)
+      if ((e = omega_draw(ctx, n, d, plan->seed, st)).st) break;
+      if ((e = dense_tc(ctx, d, n, d, 3, Yd, n, f->omega_scale, nullptr, 0, G2, d, 1, st)).st) break;
+    } else if ((e = tsprod(ctx, n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, Yd, n, G2, st)).st) {
+      break;
+    }
     // gamma = B^-T beta;  E = C'^-1;  F = B^-T E
     cudaMemcpyAsync(gamma, beta, sizeof(double) * d, cudaMemcpyDeviceToDevice, st);
     if ((e = lu_solve_dev(d, 1, f->luB, f->pivB, gamma, 1, st)).st) break;

@@ -14,7 +14,7 @@ namespace ckinv {
 namespace {
 
 template <typename T, int BM, int BN, int TM, int TN_, bool TRANSA>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN_))
+__global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 : 3)
     k_gemm(int M, int N, int K, T alpha, const T *__restrict__ A, int64_t lda, int64_t sA,
            const T *__restrict__ B, int64_t ldb, int64_t sB, T beta, T *__restrict__ C, int64_t ldc, int64_t sC,
            int ksplit) {

@@ -102,6 +102,7 @@ struct ckinv_factor {
   int32_t *cols = nullptr;   // Omega columns (copy)
   double omega_scale = 0;
   int refine_steps = 0;
+  int prec = 0;              // plan precision: FP32 keeps every contraction FP32-accurate
 };
 
 namespace ckinv {
@@ -140,6 +141,12 @@ Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams 
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
                 int64_t ldy, cudaStream_t st);
+// Tensor-core contraction of a dense FP32 matrix with Omega (the context's current draw):
+// rows i < m of A (row i at A + i*lda, contiguous over the n-long contraction), split into
+// nsplit BF16 terms.  Either Y (column-major, store) = scale * A Omega, or
+// G[i*si + j*sj] = scale * (A Omega)[i][j] reduced in FP64 (split contraction).
+Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const float *A, int64_t lda,
+               double scale, float *Y, int64_t ldy, double *G, int64_t si, int64_t sj, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- TSQR
 struct TsqrOut {

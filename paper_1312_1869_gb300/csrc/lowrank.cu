@@ -5,11 +5,7 @@
 //   K_tilde X = tau X + Q_hat B^-1 R^T Q_hat^T X    (refinement residual, FP64).
 // Long contractions over the n rows run on the CUDA cores in FP32 with FP64 accumulation
 // across 256-row chunks; every d x d operation (LU, triangular solves) is FP64.
-#include <cooperative_groups.h>
-
 #include "internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace ckinv {
 namespace {
@@ -137,76 +133,78 @@ __global__ void __launch_bounds__(256) k_tsprod_f64(int64_t n, int d1, int d2, c
     }
 }
 
-// ---------------------------------------------------------------- LU (FP64, cooperative)
-// Right-looking LU with partial pivoting of nmat d x d column-major matrices (ld = d),
-// LAPACK-style interchanges piv[j].  Block `m` (< nmat) runs the pivot step of matrix m;
-// all blocks share the rank-1 updates.  logabs[m] = sum log|U_jj|.
-__global__ void k_lu_coop(int nmat, int d, double *const *mats, int32_t *const *pivs, double *logabs,
-                          int *err) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ double sval[1024];
-  __shared__ int sidx[1024];
-  __shared__ double s_logabs;
-  if (threadIdx.x == 0) s_logabs = 0.0;
-  for (int j = 0; j < d; ++j) {
-    if ((int)blockIdx.x < nmat) {
-      double *A = mats[blockIdx.x];
-      // pivot search
-      double best = -1.0;
-      int bi = j;
-      for (int i = j + threadIdx.x; i < d; i += blockDim.x) {
-        double v = fabs(A[i + (int64_t)j * d]);
-        if (v > best) { best = v; bi = i; }
-      }
-      sval[threadIdx.x] = best;
-      sidx[threadIdx.x] = bi;
-      __syncthreads();
-      for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if ((int)threadIdx.x < off) {
-          double o = sval[threadIdx.x + off];
-          int oi = sidx[threadIdx.x + off];
-          if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-            sval[threadIdx.x] = o;
-            sidx[threadIdx.x] = oi;
-          }
-        }
-        __syncthreads();
-      }
-      const int p = sidx[0];
-      if (p != j)
-        for (int c = threadIdx.x; c < d; c += blockDim.x) {
-          double t = A[j + (int64_t)c * d];
-          A[j + (int64_t)c * d] = A[p + (int64_t)c * d];
-          A[p + (int64_t)c * d] = t;
-        }
-      __syncthreads();
-      const double piv = A[j + (int64_t)j * d];
-      if (threadIdx.x == 0) {
-        pivs[blockIdx.x][j] = p;
-        if (piv == 0.0) atomicOr(err, DERR_SINGULAR);
-        else s_logabs += log(fabs(piv));
-      }
-      const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
-      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) A[i + (int64_t)j * d] *= inv;
-      __threadfence();
+// ---------------------------------------------------------------- LU (FP64, blocked)
+// Panel step of a right-looking blocked LU with partial pivoting on nmat strided d x d
+// matrices (ld d): columns k0 .. k0+kb-1 of matrix blockIdx.x are factored (pivot search,
+// full-row interchange, scaling, rank-1 updates inside the panel); piv[j] is the LAPACK
+// interchange and logabs[m] accumulates log|U_jj|.
+__global__ void __launch_bounds__(256) k_lu_panel(int d, int k0, int kb, double *A0, int32_t *piv0, double *logabs,
+                                                  int *err) {
+  __shared__ double sval[256];
+  __shared__ int sidx[256];
+  const int m = blockIdx.x;
+  double *A = A0 + (int64_t)m * d * d;
+  int32_t *piv = piv0 + (int64_t)m * d;
+  const int tid = threadIdx.x;
+  double la = 0.0;
+  for (int j = k0; j < k0 + kb; ++j) {
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + tid; i < d; i += 256) {
+      double v = fabs(A[i + (int64_t)j * d]);
+      if (v > best) { best = v; bi = i; }
     }
-    grid.sync();
-    // rank-1 update of the trailing block of every matrix
-    const int64_t t = d - j - 1;
-    const int64_t per = t * t;
-    const int64_t total = per * nmat;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      int m = (int)(e / per);
-      int64_t w = e % per;
-      int i = j + 1 + (int)(w % t), c = j + 1 + (int)(w / t);
-      double *A = mats[m];
+    sval[tid] = best;
+    sidx[tid] = bi;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if (tid < off) {
+        double o = sval[tid + off];
+        int oi = sidx[tid + off];
+        if (o > sval[tid] || (o == sval[tid] && oi < sidx[tid])) { sval[tid] = o; sidx[tid] = oi; }
+      }
+      __syncthreads();
+    }
+    const int p = sidx[0];
+    if (p != j)
+      for (int c = tid; c < d; c += 256) {
+        double t = A[j + (int64_t)c * d];
+        A[j + (int64_t)c * d] = A[p + (int64_t)c * d];
+        A[p + (int64_t)c * d] = t;
+      }
+    __syncthreads();
+    const double pv = A[j + (int64_t)j * d];
+    if (tid == 0) {
+      piv[j] = p;
+      if (pv == 0.0) atomicOr(err, DERR_SINGULAR);
+      else la += log(fabs(pv));
+    }
+    const double inv = (pv != 0.0) ? 1.0 / pv : 0.0;
+    for (int i = j + 1 + tid; i < d; i += 256) A[i + (int64_t)j * d] *= inv;
+    __syncthreads();
+    // rank-1 update of the rest of the panel
+    const int ncol = k0 + kb - j - 1;
+    const int nrow = d - j - 1;
+    for (int e = tid; e < ncol * nrow; e += 256) {
+      int i = j + 1 + e % nrow, c = j + 1 + e / nrow;
       A[i + (int64_t)c * d] -= A[i + (int64_t)j * d] * A[j + (int64_t)c * d];
     }
-    __threadfence();
-    grid.sync();
+    __syncthreads();
   }
-  if ((int)blockIdx.x < nmat && threadIdx.x == 0) logabs[blockIdx.x] = s_logabs;
+  if (tid == 0) logabs[m] += la;
+}
+
+// A[k0:k0+kb, k0+kb:d] <- L11^-1 A[k0:k0+kb, k0+kb:d]  (L11 unit lower), one thread per column.
+__global__ void k_lu_trsm(int d, int k0, int kb, double *A0) {
+  double *A = A0 + (int64_t)blockIdx.y * d * d;
+  const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  double *col = A + (int64_t)c * d;
+  for (int i = k0 + 1; i < k0 + kb; ++i) {
+    double s = col[i];
+    for (int l = k0; l < i; ++l) s -= A[i + (int64_t)l * d] * col[l];
+    col[i] = s;
+  }
 }
 
 // ---------------------------------------------------------------- triangular solves
@@ -405,23 +403,26 @@ static Error tsprod_f64(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *
   return ok();
 }
 
-static Error lu_batch(ckinv_ctx *ctx, int nmat, int d, double **mats_h, int32_t **pivs_h, double *logabs,
-                      cudaStream_t st) {
-  double **mats = nullptr;
-  int32_t **pivs = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&mats, sizeof(double *) * nmat, st));
-  CK_CUDA(cudaMallocAsync((void **)&pivs, sizeof(int32_t *) * nmat, st));
-  CK_TRY(stage_upload(ctx, mats_h, sizeof(double *) * nmat, mats, st));
-  CK_TRY(stage_upload(ctx, pivs_h, sizeof(int32_t *) * nmat, pivs, st));
-  int per_sm = 0;
-  CK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_coop, 256, 0));
-  int grid = std::max(nmat, std::min(ctx->sm_count * std::max(per_sm, 1), ctx->sm_count));
-  int *err = ctx->d_err;
-  void *args[] = {(void *)&nmat, (void *)&d, (void *)&mats, (void *)&pivs, (void *)&logabs, (void *)&err};
-  note_launch();
-  CK_CUDA(cudaLaunchCooperativeKernel((void *)k_lu_coop, grid, 256, args, 0, st));
-  CK_CUDA(cudaFreeAsync(mats, st));
-  CK_CUDA(cudaFreeAsync(pivs, st));
+// Blocked LU of nmat strided d x d matrices: panel (one CTA per matrix), TRSM, GEMM update.
+static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv, double *logabs, cudaStream_t st) {
+  constexpr int NBL = 32;
+  CK_CUDA(cudaMemsetAsync(logabs, 0, sizeof(double) * nmat, st));
+  const int64_t sA = (int64_t)d * d;
+  for (int k0 = 0; k0 < d; k0 += NBL) {
+    const int kb = std::min(NBL, d - k0);
+    note_launch();
+    k_lu_panel<<<nmat, 256, 0, st>>>(d, k0, kb, A, piv, logabs, ctx->d_err);
+    CK_CUDA(cudaGetLastError());
+    const int rest = d - k0 - kb;
+    if (rest <= 0) continue;
+    note_launch();
+    k_lu_trsm<<<dim3((unsigned)ceil_div(rest, 128), nmat), 128, 0, st>>>(d, k0, kb, A);
+    CK_CUDA(cudaGetLastError());
+    double *L21 = A + (k0 + kb) + (int64_t)k0 * d;
+    double *U12 = A + k0 + (int64_t)(k0 + kb) * d;
+    double *A22 = A + (k0 + kb) + (int64_t)(k0 + kb) * d;
+    CK_TRY(gemm_batched<double>(ctx, false, rest, rest, kb, -1.0, L21, d, sA, U12, d, sA, 1.0, A22, d, sA, nmat, st));
+  }
   return ok();
 }
 
@@ -444,12 +445,17 @@ Error gemm_small_dev(int d, int m, const double *A, const double *Bm, double *C,
 
 Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
   const int d = f->d;
-  CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
+  // B = Omega^T Q_hat  (B^T = Q_hat^T Omega: rows of A are the columns of Q_hat).  The BF16
+  // forms use the tensor cores with Q_hat split into three BF16 terms (~3e-6 relative); the
+  // FP32 form keeps the FP32-accurate contraction (FP64 across 256-row chunks)
+  if (f->n % 4 == 0 && f->prec != CKINV_FP32)
+    CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
+  else
+    CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
   ::ckinv::note_launch(), k_make_core<<<64, 256, 0, st>>>(d, f->R, f->B, f->tau, f->Cp, f->luB, f->luC);
   CK_CUDA(cudaGetLastError());
-  double *mats[2] = {f->luB, f->luC};
-  int32_t *pivs[2] = {f->pivB, f->pivC};
-  CK_TRY(lu_batch(ctx, 2, d, mats, pivs, f->logdet_parts, st));
+  // luB and luC (and pivB, pivC) are adjacent: one strided batch of two LUs
+  CK_TRY(lu_blocked(ctx, 2, d, f->luB, f->pivB, f->logdet_parts, st));
   return ok();
 }
 

@@ -14,6 +14,7 @@
 // own TMA copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -129,20 +130,27 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
 }
 
 struct TcArgs {
-  int64_t n;
+  int64_t n;       // contraction length (points); also the row count in kernel mode
+  int64_t m;       // output rows (dense mode: rows of A)
   int dim;
   int d;
-  int num_kb;
+  int num_kb;      // 64-point blocks in total
+  int kb_per_cta;  // blocks per CTA along the contraction (split over gridDim.y)
   int stages;
   int box_rows;    // rows of Omega^T per TMA box
   KernelParams kp;
   const float *pts;
-  float *Y;
+  const float *A;  // dense mode: row i of A at A + i * lda (K-major)
+  int64_t lda;
+  float *Y;        // store mode: Y = scale * acc (column-major, ld ldy)
   int64_t ldy;
+  float *part;     // partial mode: part[split][i + j * ldp] = acc
+  int64_t ldp;
   int *err;
 };
 
-template <int NSPLIT, bool DERIV>
+// MODE 0: A = kernel tile evaluated from the points;  MODE 1: A = a dense FP32 matrix.
+template <int NSPLIT, bool DERIV, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmapB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -171,6 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = (int64_t)blockIdx.x * BM;
+  const int kb_begin = blockIdx.y * a.kb_per_cta;
+  const int nkb = max(0, min(a.num_kb, kb_begin + a.kb_per_cta) - kb_begin);
   uint32_t tmem_cols = 32;
   while ((int)tmem_cols < a.d) tmem_cols <<= 1;
 
@@ -200,15 +210,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ TMA producer (Omega)
     if (lane == 0) {
       int issued = 0;
-      for (int kb = 0; kb < a.num_kb; ++kb) {
+      for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
         mbar_arrive_expect_tx(fullB(s), b_bytes);
-        tma_load_2d(b_tile(s), &tmapB, fullB(s), kb * BK, 0);
+        const int kx = (kb_begin + kb) * BK;
+        tma_load_2d(b_tile(s), &tmapB, fullB(s), kx, 0);
         if (a.box_rows < a.d)
-          tma_load_2d(b_tile(s) + (uint32_t)a.box_rows * 128u, &tmapB, fullB(s), kb * BK,
-                      a.box_rows);
+          tma_load_2d(b_tile(s) + (uint32_t)a.box_rows * 128u, &tmapB, fullB(s), kx, a.box_rows);
         ++issued;
       }
       // every copy this CTA issued must land before its shared memory is released
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id1 = idesc_bf16(a.d > 256 ? a.d - 256 : 16);
       bool good = true;
       int issued = 0;
-      for (int kb = 0; kb < a.num_kb; ++kb) {
+      for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
         if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag)) {
@@ -260,28 +270,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ kernel-tile producers
+    // ------------------------------------------------------------ A-tile producers
     // producer warp pw = warp - 2 handles tile rows 32 (pw % 4) .. +31 and the k-half
     // pw / 4 of every 64-point block; each lane owns one row.
     const int pw = warp - 2;
     const int r = (pw & 3) * 32 + lane;
     const int h = pw >> 2;
     float4 *xw = xs_all + pw * 32;
-    const int64_t irow = min(i0 + r, a.n - 1);
+    const int64_t irow = min(i0 + r, (MODE == 0 ? a.n : a.m) - 1);
     const float cs = a.kp.coord_scale;
-    float x0 = a.pts[irow * a.dim] * cs, x1 = 0.f, x2 = 0.f;
-    if (a.dim > 1) x1 = a.pts[irow * a.dim + 1] * cs;
-    if (a.dim > 2) x2 = a.pts[irow * a.dim + 2] * cs;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (MODE == 0) {
+      x0 = a.pts[irow * a.dim] * cs;
+      if (a.dim > 1) x1 = a.pts[irow * a.dim + 1] * cs;
+      if (a.dim > 2) x2 = a.pts[irow * a.dim + 2] * cs;
+    }
+    const float *arow = (MODE == 1) ? a.A + irow * a.lda : nullptr;
+    const bool row_ok = (MODE == 1) ? (i0 + r < a.m) : true;
     const int kind = a.kp.kind;
     const float inv_l = a.kp.inv_l;
     const uint32_t rowbase = (uint32_t)r * 128u;
     const uint32_t swz = (uint32_t)(r & 7);
     bool good = true;
-    for (int kb = 0; kb < a.num_kb; ++kb) {
+    for (int kb = 0; kb < nkb; ++kb) {
       int s = kb % S;
       uint32_t ph = (uint32_t)(kb / S) & 1u;
-      {
-        int64_t k = (int64_t)kb * BK + h * 32 + lane;
+      const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * 32;
+      if (MODE == 0) {
+        int64_t k = kbase + lane;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < a.n) {
           v.x = a.pts[k * a.dim] * cs;
@@ -298,13 +314,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float kv[8];
+        if (MODE == 0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float4 p = xw[c * 8 + u];
-          float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
-          float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          float v = dev::kernel_value(kind, r2, inv_l, DERIV);
-          kv[u] = (p.w != 0.0f) ? v : 0.0f;
+          for (int u = 0; u < 8; ++u) {
+            float4 p = xw[c * 8 + u];
+            float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
+            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            float v = dev::kernel_value(kind, r2, inv_l, DERIV);
+            kv[u] = (p.w != 0.0f) ? v : 0.0f;
+          }
+        } else {
+          const int64_t k0 = kbase + c * 8;
+          if (row_ok && k0 + 8 <= a.n) {
+            float4 lo = *reinterpret_cast<const float4 *>(arow + k0);
+            float4 hi = *reinterpret_cast<const float4 *>(arow + k0 + 4);
+            kv[0] = lo.x; kv[1] = lo.y; kv[2] = lo.z; kv[3] = lo.w;
+            kv[4] = hi.x; kv[5] = hi.y; kv[6] = hi.z; kv[7] = hi.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) kv[u] = (row_ok && k0 + u < a.n) ? arow[k0 + u] : 0.0f;
+          }
         }
         const uint32_t chunk = (uint32_t)(h * 4 + c);
         const uint32_t off = rowbase + ((chunk ^ swz) << 4);
@@ -332,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(fullA(s));
     }
     // ------------------------------------------------------------ epilogue
-    bool e_ok = good && mbar_wait(accum_bar, 0u, abort_flag);
+    bool e_ok = good && nkb > 0 && mbar_wait(accum_bar, 0u, abort_flag);
     if (__all_sync(0xffffffffu, e_ok)) {
       tc_fence_after();
       const int q = warp & 3;                 // TMEM lane quadrant this warp may access
@@ -340,12 +369,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int cols_half = a.d / 2;
       const int64_t i = i0 + q * 32 + lane;
       const float scale = (float)a.kp.scale;
+      const int64_t mrows = (MODE == 0) ? a.n : a.m;
+      float *pout = a.part ? a.part + (int64_t)blockIdx.y * a.ldp * a.d : nullptr;
       for (int j = half * cols_half; j < (half + 1) * cols_half; j += 8) {
         float v[8];
         tmem_ld8(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)j, v);
-        if (i < a.n) {
+        if (i < mrows) {
+          if (pout) {
 #pragma unroll
-          for (int t = 0; t < 8; ++t) a.Y[i + (int64_t)(j + t) * a.ldy] = v[t] * scale;
+            for (int t = 0; t < 8; ++t) pout[i + (int64_t)(j + t) * a.ldp] = nkb > 0 ? v[t] : 0.0f;
+          } else {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a.Y[i + (int64_t)(j + t) * a.ldy] = v[t] * scale;
+          }
         }
       }
     }
@@ -373,64 +409,133 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-template <int NSPLIT, bool DERIV>
-Error launch(const CUtensorMap &map, const TcArgs &a, size_t smem, int grid, cudaStream_t st) {
-  auto kfn = k_sketch_tc<NSPLIT, DERIV>;
+template <int NSPLIT, bool DERIV, int MODE>
+Error launch(const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid, cudaStream_t st) {
+  auto kfn = k_sketch_tc<NSPLIT, DERIV, MODE>;
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ::ckinv::note_launch(), kfn<<<grid, kThreads, smem, st>>>(map, a);
+  ::ckinv::note_launch();
+  kfn<<<grid, kThreads, smem, st>>>(map, a);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
 
-}  // namespace
-
-Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const KernelParams &kp,
-                const float *points, bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+// Tensor map over the BF16 Omega^T of the context and the launch geometry.
+Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, size_t *smem) {
   if (d % 16 != 0 || d > 512 || d < 16) return fail(CKINV_EINVAL, "sketch_tc: d must be 16..512, d % 16 == 0");
-  CK_TRY(omega_materialise_bf16(ctx, st));
+  if (nsplit < 1 || nsplit > 3) return fail(CKINV_EINVAL, "sketch_tc: 1..3 BF16 terms");
   const OmegaCache &om = ctx->om;
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return fail(CKINV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
   const int box_rows = d <= 256 ? d : d / 2;
-  CUtensorMap map;
   cuuint64_t gdim[2] = {(cuuint64_t)om.kpad, (cuuint64_t)d};
   cuuint64_t gstride[1] = {(cuuint64_t)om.kpad * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)om.omegaT, gdim, gstride, box,
-                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)om.omegaT, gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(CKINV_ECUDA, "cuTensorMapEncodeTiled failed");
-
-  TcArgs a;
-  a.n = n;
-  a.dim = dim;
-  a.d = d;
-  a.num_kb = (int)(om.kpad / BK);
-  a.box_rows = box_rows;
-  a.kp = kp;
-  a.pts = points;
-  a.Y = Y;
-  a.ldy = ldy;
-  a.err = ctx->d_err;
+  memset(a, 0, sizeof(*a));
+  a->d = d;
+  a->num_kb = (int)(om.kpad / BK);
+  a->kb_per_cta = a->num_kb;
+  a->box_rows = box_rows;
+  a->err = ctx->d_err;
   const size_t stage_bytes = (size_t)nsplit * kATileBytes + (size_t)d * BK * 2;
   const size_t head = 512 + 8 * 32 * 16 + 1024;   // barriers, point buffers, alignment slack
   const size_t limit = 227 * 1024;
   int S = (int)((limit - head) / stage_bytes);
   if (S > 4) S = 4;
   if (S < 1) return fail(CKINV_EUNSUPPORTED, "sketch_tc: stage does not fit in shared memory");
-  a.stages = S;
-  const size_t smem = head + (size_t)S * stage_bytes;
-  const int grid = (int)ceil_div(n, BM);
+  a->stages = S;
+  *smem = head + (size_t)S * stage_bytes;
+  return ok();
+}
+
+template <int MODE>
+Error dispatch(int nsplit, bool deriv, const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid,
+               cudaStream_t st) {
   switch (nsplit * 2 + (deriv ? 1 : 0)) {
-    case 2: return launch<1, false>(map, a, smem, grid, st);
-    case 3: return launch<1, true>(map, a, smem, grid, st);
-    case 4: return launch<2, false>(map, a, smem, grid, st);
-    case 5: return launch<2, true>(map, a, smem, grid, st);
-    case 6: return launch<3, false>(map, a, smem, grid, st);
-    case 7: return launch<3, true>(map, a, smem, grid, st);
+    case 2: return launch<1, false, MODE>(map, a, smem, grid, st);
+    case 3: return launch<1, true, MODE>(map, a, smem, grid, st);
+    case 4: return launch<2, false, MODE>(map, a, smem, grid, st);
+    case 5: return launch<2, true, MODE>(map, a, smem, grid, st);
+    case 6: return launch<3, false, MODE>(map, a, smem, grid, st);
+    case 7: return launch<3, true, MODE>(map, a, smem, grid, st);
   }
   return fail(CKINV_EINVAL, "sketch_tc: nsplit must be 1..3");
+}
+
+// G[i * si + j * sj] = scale * sum_s part[s][i + j * ldp]   (FP64 sum over the splits)
+__global__ void k_reduce_parts(int m, int d, int splits, const float *part, int64_t ldp, double scale, double *G,
+                               int64_t si, int64_t sj) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)m * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % m, j = e / m;
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += (double)part[(int64_t)s * ldp * d + i + j * ldp];
+    G[i * si + j * sj] = scale * acc;
+  }
+}
+
+}  // namespace
+
+Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const KernelParams &kp, const float *points,
+                bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+  CK_TRY(omega_materialise_bf16(ctx, st));
+  CUtensorMap map;
+  TcArgs a;
+  size_t smem = 0;
+  CK_TRY(prepare(ctx, d, nsplit, &map, &a, &smem));
+  a.n = n;
+  a.m = n;
+  a.dim = dim;
+  a.kp = kp;
+  a.pts = points;
+  a.Y = Y;
+  a.ldy = ldy;
+  return dispatch<0>(nsplit, deriv, map, a, smem, dim3((unsigned)ceil_div(n, BM), 1), st);
+}
+
+Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const float *A, int64_t lda, double scale,
+               float *Y, int64_t ldy, double *G, int64_t si, int64_t sj, cudaStream_t st) {
+  if (lda % 4 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+    return fail(CKINV_EINVAL, "dense_tc: A must be 16-byte aligned with lda % 4 == 0");
+  CK_TRY(omega_materialise_bf16(ctx, st));
+  CUtensorMap map;
+  TcArgs a;
+  size_t smem = 0;
+  CK_TRY(prepare(ctx, d, nsplit, &map, &a, &smem));
+  a.n = n;
+  a.m = m;
+  a.A = A;
+  a.lda = lda;
+  a.kp.scale = scale;
+  const int mt = (int)ceil_div(m, BM);
+  if (Y) {
+    a.Y = Y;
+    a.ldy = ldy;
+    return dispatch<1>(nsplit, false, map, a, smem, dim3(mt, 1), st);
+  }
+  // split the contraction so that the grid covers every SM, then reduce in FP64
+  int splits = std::max(1, std::min(a.num_kb, (ctx->sm_count + mt - 1) / mt));
+  a.kb_per_cta = (int)ceil_div(a.num_kb, splits);
+  splits = (int)ceil_div(a.num_kb, a.kb_per_cta);
+  const int64_t ldp = (int64_t)mt * BM;
+  float *part = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(float) * (size_t)splits * ldp * d, st));
+  a.part = part;
+  a.ldp = ldp;
+  Error e = dispatch<1>(nsplit, false, map, a, smem, dim3(mt, splits), st);
+  if (e.st == CKINV_OK) {
+    note_launch();
+    k_reduce_parts<<<(unsigned)std::min<int64_t>(ceil_div(m * d, 256), 2048), 256, 0, st>>>(
+        (int)m, d, splits, part, ldp, scale, G, si, sj);
+    cudaError_t c = cudaGetLastError();
+    if (c != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(c));
+  }
+  cudaFreeAsync(part, st);
+  return e;
 }
 
 }  // namespace ckinv

@@ -53,14 +53,22 @@ __device__ __forceinline__ void block_sum(T (&vals)[NV], T *red, T *out) {
 // Householder QR of the panel M[c0:H, c0:c0+NB] of problem blockIdx.x (M: H x d, ld H).
 // Writes R and the reflectors into M, the explicit reflectors (unit diagonal, zeros above)
 // into Vx[:, c0:c0+NB], and the panel's compact-WY block into Tm[c0:c0+NB, c0:c0+NB].
+// Stacked mode (a combine, H = 2d, M = [R_a; R_b] with both upper triangular): the
+// structurally nonzero rows of the panel are the top rows c0..c0+NB-1 and the bottom rows
+// 0..c0+NB-1 (physical rows d..d+c0+NB-1); only those are loaded and factored.
 template <typename T>
-__global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H, int d, int c0) {
+__device__ __forceinline__ int panel_row(bool stacked, int c0, int d, int r) {
+  return stacked ? (r < NB ? c0 + r : d + r - NB) : c0 + r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H, int d, int c0, int stacked) {
   extern __shared__ __align__(16) uint8_t sm_raw[];
   const int64_t pslot = (int64_t)H * d;
   M += blockIdx.x * pslot;
   Vx += blockIdx.x * pslot;
   Tm += (int64_t)blockIdx.x * d * d;
-  const int h = H - c0;
+  const int h = stacked ? c0 + 2 * NB : H - c0;
   const int hp = h | 1;
   T *Ps = reinterpret_cast<T *>(sm_raw);                  // NB x hp
   T *red = Ps + NB * hp;                                  // 16 warps x NB
@@ -69,10 +77,11 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
   T *Ts = wv + NB;                                        // NB x NB
   T *scal = Ts + NB * NB;                                 // [tau, rdiag, head]
   const int tid = threadIdx.x;
-  T *base = M + c0 + (int64_t)c0 * H;                     // logical row r <-> row c0 + r
+  T *base = M + (int64_t)c0 * H;                          // column c0
 
   for (int c = 0; c < NB; ++c)
-    for (int r = tid; r < h; r += PF_THREADS) Ps[c * hp + r] = base[r + (int64_t)c * H];
+    for (int r = tid; r < h; r += PF_THREADS)
+      Ps[c * hp + r] = base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H];
   for (int e = tid; e < NB * NB; e += PF_THREADS) Ts[e] = 0;
   __syncthreads();
 
@@ -125,10 +134,12 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
   for (int c = 0; c < NB; ++c) {
     T *vcol = Vx + (int64_t)(c0 + c) * H;
     for (int r = tid; r < H; r += PF_THREADS) {
-      int lr = r - c0;
-      vcol[r] = (lr < c) ? T(0) : (lr == c ? T(1) : Ps[c * hp + lr]);
+      int lr;                                   // logical panel row of physical row r, or -1
+      if (stacked) lr = (r >= c0 && r < c0 + NB) ? r - c0 : ((r >= d && r < d + c0 + NB) ? r - d + NB : -1);
+      else lr = r - c0;
+      vcol[r] = (lr < 0 || lr < c) ? T(0) : (lr == c ? T(1) : Ps[c * hp + lr]);
     }
-    for (int r = tid; r < h; r += PF_THREADS) base[r + (int64_t)c * H] = Ps[c * hp + r];
+    for (int r = tid; r < h; r += PF_THREADS) base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H] = Ps[c * hp + r];
   }
   for (int e = tid; e < NB * NB; e += PF_THREADS) {
     int i = e / NB, j = e % NB;              // Ts is row-major [i][j]; Tm column-major
@@ -226,20 +237,46 @@ __global__ void k_leaf_q(const T *Qs, int H, int d, const int64_t *row0, const i
   }
 }
 
+// dst_b = alpha * src_b + beta * dst_b on an m x n block (column-major, strided batches).
+template <typename T>
+__global__ void k_axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta, T *dst, int64_t ldd,
+                        int64_t sd, int batch) {
+  const int64_t per = (int64_t)m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = e / per, w = e % per;
+    int64_t r = w % m, c = w / m;
+    T *o = dst + b * sd + r + c * ldd;
+    T v = alpha * src[b * ss + r + c * lds];
+    *o = (beta == T(0)) ? v : v + beta * *o;
+  }
+}
+
+template <typename T>
+Error axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta, T *dst, int64_t ldd, int64_t sd,
+            int batch, cudaStream_t st) {
+  unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)m * n * batch, 256), 4096);
+  note_launch();
+  k_axpby<T><<<g, 256, 0, st>>>(m, n, alpha, src, lds, ss, beta, dst, ldd, sd, batch);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
 // One stage: P independent QRs of H x d matrices (strided, ld H).
 template <typename T>
 struct Stage {
   int P = 0, H = 0;
+  bool stacked = false;                 // a combine stage: M = [R_a; R_b], H = 2d
   T *M = nullptr, *Vx = nullptr, *Tm = nullptr;
   int *top = nullptr, *bot = nullptr;   // device slot indices (combines); top = slot for leaves
 };
 
 template <typename T>
 Error run_panel(const Stage<T> &s, int d, int c0, cudaStream_t st) {
-  size_t smem = panel_smem<T>(s.H - c0);
+  size_t smem = panel_smem<T>(s.stacked ? c0 + 2 * NB : s.H - c0);
   CK_CUDA(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   note_launch();
-  k_panel<T><<<s.P, PF_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0);
+  k_panel<T><<<s.P, PF_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0, s.stacked ? 1 : 0);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
@@ -253,6 +290,31 @@ Error rqr(const ckinv_ctx *ctx, const Stage<T> &s, int d, int c0, int w, T *W, T
   const int H = s.H, P = s.P;
   const int64_t sM = (int64_t)H * d, sT = (int64_t)d * d, sW = (int64_t)wl * wr;
   CK_TRY(rqr<T>(ctx, s, d, c0, wl, W, W2, st));
+  if (s.stacked) {
+    // Stacked triangles: V1 = [I (top rows c0..c0+wl); V1_bot (bottom rows 0..c0+wl)],
+    // C2's active rows are top c0..c0+w and bottom 0..c0+w.
+    const int Kb = c0 + wl;
+    T *V1b = s.Vx + d + (int64_t)c0 * H;
+    T *C2t = s.M + c0 + (int64_t)(c0 + wl) * H;
+    T *C2b = s.M + d + (int64_t)(c0 + wl) * H;
+    T *T11 = s.Tm + c0 + (int64_t)c0 * d;
+    // W = C2_top[0:wl] + V1_bot^T C2_bot ; W2 = T11^T W
+    CK_TRY(axpby<T>(wl, wr, T(1), C2t, H, sM, T(0), W, wl, sW, P, st));
+    CK_TRY(gemm_batched<T>(ctx, true, wl, wr, Kb, T(1), V1b, H, sM, C2b, H, sM, T(1), W, wl, sW, P, st));
+    CK_TRY(gemm_batched<T>(ctx, true, wl, wr, wl, T(1), T11, d, sT, W, wl, sW, T(0), W2, wl, sW, P, st));
+    // C2_top[0:wl] -= W2 ; C2_bot -= V1_bot W2
+    CK_TRY(axpby<T>(wl, wr, T(-1), W2, wl, sW, T(1), C2t, H, sM, P, st));
+    CK_TRY(gemm_batched<T>(ctx, false, Kb, wr, wl, T(-1), V1b, H, sM, W2, wl, sW, T(1), C2b, H, sM, P, st));
+    CK_TRY(rqr<T>(ctx, s, d, c0 + wl, wr, W, W2, st));
+    // T12 = -T11 (V1_bot^T V2_bot) T22   (the identity parts of V1 and V2 do not overlap)
+    T *V2b = s.Vx + d + (int64_t)(c0 + wl) * H;
+    T *T22 = s.Tm + (c0 + wl) + (int64_t)(c0 + wl) * d;
+    T *T12 = s.Tm + c0 + (int64_t)(c0 + wl) * d;
+    CK_TRY(gemm_batched<T>(ctx, true, wl, wr, Kb, T(1), V1b, H, sM, V2b, H, sM, T(0), W, wl, sW, P, st));
+    CK_TRY(gemm_batched<T>(ctx, false, wl, wr, wl, T(1), T11, d, sT, W, wl, sW, T(0), W2, wl, sW, P, st));
+    CK_TRY(gemm_batched<T>(ctx, false, wl, wr, wr, T(-1), W2, wl, sW, T22, d, sT, T(0), T12, d, sT, P, st));
+    return ok();
+  }
   const int K = H - c0;
   T *V1 = s.Vx + c0 + (int64_t)c0 * H;              // rows c0.., columns c0 .. c0+wl
   T *C2 = s.M + c0 + (int64_t)(c0 + wl) * H;        // rows c0.., columns c0+wl .. c0+w
@@ -282,6 +344,13 @@ Error apply_q(const ckinv_ctx *ctx, const Stage<T> &s, int d, const double *Xslo
   note_launch();
   k_init_qs<T><<<g, 256, 0, st>>>(Xslot, s.top, H, d, Qs);
   CK_CUDA(cudaGetLastError());
+  if (s.stacked) {
+    // V = [I; V_bot]:  Z2 = T X ;  top = X - Z2 ;  bottom = -V_bot Z2
+    CK_TRY(gemm_batched<T>(ctx, false, d, d, d, T(1), s.Tm, d, sD, Qs, H, sM, T(0), Z2, d, sD, P, st));
+    CK_TRY(axpby<T>(d, d, T(-1), Z2, d, sD, T(1), Qs, H, sM, P, st));
+    CK_TRY(gemm_batched<T>(ctx, false, d, d, d, T(-1), s.Vx + d, H, sM, Z2, d, sD, T(0), Qs + d, H, sM, P, st));
+    return ok();
+  }
   CK_TRY(gemm_batched<T>(ctx, true, d, d, d, T(1), s.Vx, H, sM, Qs, H, sM, T(0), Z1, d, sD, P, st));
   CK_TRY(gemm_batched<T>(ctx, false, d, d, d, T(1), s.Tm, d, sD, Z1, d, sD, T(0), Z2, d, sD, P, st));
   CK_TRY(gemm_batched<T>(ctx, false, H, d, d, T(-1), s.Vx, H, sM, Z2, d, sD, T(1), Qs, H, sM, P, st));
@@ -415,11 +484,13 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
       dim3 g((unsigned)std::min<int64_t>(ceil_div(2LL * d * d, 256), 256), P);
       if (lv.fp64) {
         if ((e = alloc_stage<double>(sd[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
+        sd[l].stacked = true;
         note_launch();
         k_build_stack<double><<<g, 256, 0, st>>>(Rslot, sd[l].top, sd[l].bot, d, sd[l].M);
         e = factor_stage<double>(ctx, sd[l], d, Rslot, st);
       } else {
         if ((e = alloc_stage<float>(sf[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
+        sf[l].stacked = true;
         note_launch();
         k_build_stack<float><<<g, 256, 0, st>>>(Rslot, sf[l].top, sf[l].bot, d, sf[l].M);
         e = factor_stage<float>(ctx, sf[l], d, Rslot, st);

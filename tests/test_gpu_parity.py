@@ -93,15 +93,20 @@ def test_derivative_sketch_matches_oracle(ctx, prec, tol, kind):
     assert rel(host(Yd), Yo) <= tol
 
 
-def test_dense_sketch_matches_oracle(ctx):
-    n, d = 1536, 64
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16x2", 3e-5), ("bf16", 4e-3)])
+@pytest.mark.parametrize("n,d", [(1536, 64), (1000, 272)])
+def test_dense_sketch_matches_oracle(ctx, prec, tol, n, d):
+    """Materialised K (the plain-method workload with K in HBM): SIMT FP32 or tensor cores."""
     pts = synth.points(n, 3, 2).astype(np.float64)
     K = okk.kernel_matrix(pts, pts, okk.MATERN52, 0.15, 1.0)
-    plan = ck.Plan(n=n, d=d, dim=3, seed=0)
+    plan = ck.Plan(n=n, d=d, dim=3, seed=0, prec=ck.PRECISIONS[prec])
     Y = ck.sketch(ctx, plan, ck.Kernel(ck.DENSE, 0, 0, 1e-5), K=col(K))
     torch.cuda.synchronize()
+    ck.check(ctx)
     Yo = osk.sketch_dense(K.astype(np.float32).astype(np.float64), oom.omega_matrix(n, d, 0))
-    assert rel(host(Y), Yo) <= 1e-5
+    err = rel(host(Y), Yo)
+    print("dense sketch %s n=%d d=%d err=%.3e" % (prec, n, d, err))
+    assert err <= tol
 
 
 # ------------------------------------------------------------------------- TSQR
