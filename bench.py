@@ -316,7 +316,7 @@ def main():
     ap.add_argument("--workload", default="c3_bf16_n262144")
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x2", "bf16x3"])
     ap.add_argument("--refine", type=int, default=1)
-    ap.add_argument("--fp64-levels", type=int, default=1)
+    ap.add_argument("--fp64-levels", type=int, default=0)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--forms", action="store_true", help="also time the BF16x2, BF16x3 and FP32 forms once")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -88,20 +88,34 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
     }
 }
 
-// G = Q^T X with FP64 arithmetic (Q FP32 n x d, X FP32 n x m): the products of two FP32
-// numbers are exact in FP64, so this is the residual-grade contraction of the refinement.
-__global__ void __launch_bounds__(256) k_tsprod_f64(int64_t n, int d1, int d2, const float *__restrict__ L,
-                                                    int64_t ldl, const float *__restrict__ M, int64_t ldm,
-                                                    double *G, int64_t rows_per_split) {
+// ---------------------------------------------------------------- residual-grade sums
+// Products of two FP32 numbers are split exactly into p + e (p = fl(ab), e = fma(a, b, -p));
+// the p's are summed with TwoSum compensation and the e's plainly (they are 2^-24 smaller),
+// and each 256-row chunk is folded into FP64.  This gives sums accurate to about 2^-48 at
+// FP32 throughput, for the residual of the FP64 refinement step.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &err) {
+  s = a + b;
+  float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+}
+
+// G (d1 x d2, FP64, ld d1) += L^T M over rows [rb, re) (L, M FP32), compensated.
+__global__ void __launch_bounds__(256) k_tsprod_dd(int64_t n, int d1, int d2, const float *__restrict__ L,
+                                                   int64_t ldl, const float *__restrict__ M, int64_t ldm,
+                                                   double *G, int64_t rows_per_split) {
   __shared__ float Ls[32][64 + 4];
   __shared__ float Ms[32][32 + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // 64 x 32 tile: 4 x 2 per thread
   const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
   const int64_t rb = (int64_t)blockIdx.z * rows_per_split;
   const int64_t re = min(n, rb + rows_per_split);
+  float hs[4][2], lc[4][2];
   double acc[4][2];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) { acc[a][0] = 0.0; acc[a][1] = 0.0; }
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) { hs[a][b] = 0.f; lc[a][b] = 0.f; acc[a][b] = 0.0; }
+  int step = 0;
   for (int64_t k0 = rb; k0 < re; k0 += 32) {
     for (int e = tid; e < 32 * 64; e += 256) {
       int kk = e % 32, c = e / 32;
@@ -114,22 +128,89 @@ __global__ void __launch_bounds__(256) k_tsprod_f64(int64_t n, int d1, int d2, c
       Ms[kk][c] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
     }
     __syncthreads();
+#pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
+      float b0 = Ms[kk][tx * 2], b1 = Ms[kk][tx * 2 + 1];
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        double a = (double)Ls[kk][ty * 4 + x];
-        acc[x][0] = fma(a, (double)Ms[kk][tx * 2], acc[x][0]);
-        acc[x][1] = fma(a, (double)Ms[kk][tx * 2 + 1], acc[x][1]);
+        float a = Ls[kk][ty * 4 + x];
+        float p0 = a * b0, e0 = fmaf(a, b0, -p0);
+        float p1 = a * b1, e1 = fmaf(a, b1, -p1);
+        float s0, r0, s1, r1;
+        two_sum(hs[x][0], p0, s0, r0);
+        two_sum(hs[x][1], p1, s1, r1);
+        hs[x][0] = s0; lc[x][0] += r0 + e0;
+        hs[x][1] = s1; lc[x][1] += r1 + e1;
       }
     }
     __syncthreads();
+    if (++step == 8) {
+      step = 0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          acc[x][y] += (double)hs[x][y] + (double)lc[x][y];
+          hs[x][y] = 0.f;
+          lc[x][y] = 0.f;
+        }
+    }
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 2; ++y) {
       int i = i0 + ty * 4 + x, j = j0 + tx * 2 + y;
-      if (i < d1 && j < d2) atomicAdd(&G[i + (int64_t)j * d1], acc[x][y]);
+      if (i < d1 && j < d2) atomicAdd(&G[i + (int64_t)j * d1], acc[x][y] + (double)hs[x][y] + (double)lc[x][y]);
+    }
+}
+
+// r = A - tau X - Q S  (Q FP32 n x d, S FP64 d x m), compensated FP32 sums, FP64 combination.
+__global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, const float *__restrict__ Q,
+                                                     int64_t ldq, const double *__restrict__ S,
+                                                     const float *__restrict__ A, int64_t lda,
+                                                     const float *__restrict__ X, int64_t ldx, double tau, float *Rs,
+                                                     int64_t ldr) {
+  __shared__ float Sh[64][17], Sl[64][17];
+  const int tid = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 256 + tid;
+  const int c0 = blockIdx.y * 16;
+  const int mc = min(16, m - c0);
+  float hs[16], lc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) { hs[c] = 0.f; lc[c] = 0.f; }
+  for (int k0 = 0; k0 < d; k0 += 64) {
+    __syncthreads();
+    for (int e = tid; e < 64 * 16; e += 256) {
+      int kk = e % 64, c = e / 64;
+      double v = (k0 + kk < d && c < mc) ? S[(k0 + kk) + (int64_t)(c0 + c) * d] : 0.0;
+      float hi = (float)v;
+      Sh[kk][c] = hi;
+      Sl[kk][c] = (float)(v - (double)hi);
+    }
+    __syncthreads();
+    if (i < n) {
+      int kmax = min(64, d - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        float q = Q[i + (int64_t)(k0 + kk) * ldq];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float hi = Sh[kk][c];
+          float p = q * hi, e = fmaf(q, hi, -p);
+          float s, r;
+          two_sum(hs[c], p, s, r);
+          hs[c] = s;
+          lc[c] += r + fmaf(q, Sl[kk][c], e);
+        }
+      }
+    }
+  }
+  if (i < n)
+    for (int c = 0; c < mc; ++c) {
+      double qs = (double)hs[c] + (double)lc[c];
+      double a = (double)A[i + (int64_t)(c0 + c) * lda];
+      double x = (double)X[i + (int64_t)(c0 + c) * ldx];
+      Rs[i + (int64_t)(c0 + c) * ldr] = (float)(a - tau * x - qs);
     }
 }
 
@@ -320,46 +401,6 @@ __global__ void __launch_bounds__(256) k_apply_x(int64_t n, int d, int m, const 
       X[i + (int64_t)(c0 + c) * ldx] = (A[i + (int64_t)(c0 + c) * lda] - acc[c]) * inv_tau;
 }
 
-// r = A - tau X - Q S  in FP64 (Q FP32, S FP64 d x m); r written as FP32 pair? no: FP32
-// is enough for the right-hand side of the correction solve once the cancellation has
-// happened in FP64.
-__global__ void __launch_bounds__(256) k_residual(int64_t n, int d, int m, const float *__restrict__ Q,
-                                                  int64_t ldq, const double *__restrict__ S,
-                                                  const float *__restrict__ A, int64_t lda,
-                                                  const float *__restrict__ X, int64_t ldx, double tau,
-                                                  float *Rs, int64_t ldr) {
-  __shared__ double Ss[64][33];
-  const int tid = threadIdx.x;
-  const int64_t i = (int64_t)blockIdx.x * 256 + tid;
-  const int c0 = blockIdx.y * 32;
-  const int mc = min(32, m - c0);
-  double acc[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-  for (int k0 = 0; k0 < d; k0 += 64) {
-    __syncthreads();
-    for (int e = tid; e < 64 * 32; e += 256) {
-      int kk = e % 64, c = e / 64;
-      Ss[kk][c] = (k0 + kk < d && c < mc) ? S[(k0 + kk) + (int64_t)(c0 + c) * d] : 0.0;
-    }
-    __syncthreads();
-    if (i < n) {
-      int kmax = min(64, d - k0);
-      for (int kk = 0; kk < kmax; ++kk) {
-        double q = (double)Q[i + (int64_t)(k0 + kk) * ldq];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fma(q, Ss[kk][c], acc[c]);
-      }
-    }
-  }
-  if (i < n)
-    for (int c = 0; c < mc; ++c) {
-      double a = (double)A[i + (int64_t)(c0 + c) * lda];
-      double x = (double)X[i + (int64_t)(c0 + c) * ldx];
-      Rs[i + (int64_t)(c0 + c) * ldr] = (float)(a - tau * x - acc[c]);
-    }
-}
-
 __global__ void k_add_inplace(int64_t n, int m, float *X, int64_t ldx, const float *D, int64_t ldd) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -390,15 +431,15 @@ Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t 
   return ok();
 }
 
-static Error tsprod_f64(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const float *M,
-                        int64_t ldm, double *G, cudaStream_t st) {
+static Error tsprod_dd(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const float *M,
+                       int64_t ldm, double *G, cudaStream_t st) {
   CK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)d1 * d2, st));
   int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 32);
   int sp = splits_for(ctx, n, tx * ty);
-  int64_t rps = ceil_div(ceil_div(n, sp), 32) * 32;
+  int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
   dim3 grid(tx, ty, sp);
-  ::ckinv::note_launch(), k_tsprod_f64<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, G, rps);
+  ::ckinv::note_launch(), k_tsprod_dd<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, G, rps);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
@@ -494,13 +535,13 @@ Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64
     CK_CUDA(cudaMallocAsync((void **)&Dx, sizeof(float) * n * m, st));
     for (int s = 0; s < refine_steps; ++s) {
       // S = B^-1 R^T Q^T X  (FP64)
-      CK_TRY(tsprod_f64(ctx, n, d, m, f->Q, n, X, ldx, Z, st));
+      CK_TRY(tsprod_dd(ctx, n, d, m, f->Q, n, X, ldx, Z, st));
       dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
       ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);
       CK_CUDA(cudaGetLastError());
       CK_TRY(lu_solve(d, m, f->luB, f->pivB, W, 0, st));
-      dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 32));
-      ::ckinv::note_launch(), k_residual<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, Ain, lda, X, ldx, f->tau, Rs, n);
+      dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 16));
+      ::ckinv::note_launch(), k_residual_dd<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, Ain, lda, X, ldx, f->tau, Rs, n);
       CK_CUDA(cudaGetLastError());
       CK_TRY(solve_into(Rs, n, Dx, n));
       ::ckinv::note_launch(), k_add_inplace<<<(unsigned)std::min<int64_t>(ceil_div(n * m, 256), 65535), 256, 0, st>>>(n, m, X, ldx, Dx, n);

@@ -44,13 +44,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
       "r"(bytes)
       : "memory");
 }
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
+// hint (ns) elapses, instead of spinning on the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
@@ -61,19 +63,27 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Bounded wait: gives up after ~1 s or when another warp has flagged an abort.
 __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  uint64_t t0 = 0;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
+    if ((it & 15u) == 15u) {
       if (*abort_flag) return false;
-      uint64_t now = global_ns();
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > 1000000000ull) {
+      if (global_ns() - t0 > 1000000000ull) {
         *abort_flag = 1;
         return false;
       }
     }
   }
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the warp agrees on the outcome.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -292,36 +302,51 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t rowbase = (uint32_t)r * 128u;
     const uint32_t swz = (uint32_t)(r & 7);
     bool good = true;
+    // the point this lane stages for the next block, fetched one block ahead
+    auto load_point = [&](int kb) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      int64_t k = (int64_t)(kb_begin + kb) * BK + h * 32 + lane;
+      if (MODE == 0 && kb < nkb && k < a.n) {
+        v.x = a.pts[k * a.dim] * cs;
+        if (a.dim > 1) v.y = a.pts[k * a.dim + 1] * cs;
+        if (a.dim > 2) v.z = a.pts[k * a.dim + 2] * cs;
+        v.w = 1.0f;                        // marks a real point
+      }
+      return v;
+    };
+    float4 pnext = load_point(0);
     for (int kb = 0; kb < nkb; ++kb) {
       int s = kb % S;
       uint32_t ph = (uint32_t)(kb / S) & 1u;
       const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * 32;
+      const bool full_block = (kbase + 32 <= (MODE == 0 ? a.n : a.n));
       if (MODE == 0) {
-        int64_t k = kbase + lane;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < a.n) {
-          v.x = a.pts[k * a.dim] * cs;
-          if (a.dim > 1) v.y = a.pts[k * a.dim + 1] * cs;
-          if (a.dim > 2) v.z = a.pts[k * a.dim + 2] * cs;
-          v.w = 1.0f;                      // marks a real point
-        }
         __syncwarp();                      // previous block's reads of xw are done
-        xw[lane] = v;
+        xw[lane] = pnext;
         __syncwarp();
+        pnext = load_point(kb + 1);
       }
-      bool w_ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
-      if (!__all_sync(0xffffffffu, w_ok)) { good = false; break; }
+      if (!mbar_wait_warp(empty(s), ph ^ 1u, abort_flag)) { good = false; break; }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float kv[8];
         if (MODE == 0) {
+          if (full_block && a.dim <= 2) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            float4 p = xw[c * 8 + u];
-            float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
-            float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            float v = dev::kernel_value(kind, r2, inv_l, DERIV);
-            kv[u] = (p.w != 0.0f) ? v : 0.0f;
+            for (int u = 0; u < 8; ++u) {
+              float4 p = xw[c * 8 + u];
+              float dx = x0 - p.x, dy = x1 - p.y;
+              kv[u] = dev::kernel_value(kind, fmaf(dy, dy, dx * dx), inv_l, DERIV);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              float4 p = xw[c * 8 + u];
+              float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
+              float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              float v = dev::kernel_value(kind, r2, inv_l, DERIV);
+              kv[u] = (p.w != 0.0f) ? v : 0.0f;
+            }
           }
         } else {
           const int64_t k0 = kbase + c * 8;
@@ -361,8 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(fullA(s));
     }
     // ------------------------------------------------------------ epilogue
-    bool e_ok = good && nkb > 0 && mbar_wait(accum_bar, 0u, abort_flag);
-    if (__all_sync(0xffffffffu, e_ok)) {
+    bool e_ok = good && nkb > 0 && mbar_wait_warp(accum_bar, 0u, abort_flag);
+    if (e_ok) {
       tc_fence_after();
       const int q = warp & 3;                 // TMEM lane quadrant this warp may access
       const int half = pw >> 2;               // two warps per quadrant split the columns

@@ -26,6 +26,14 @@ size_t panel_smem(int h) {
   return sizeof(T) * ((size_t)NB * hp + (PF_THREADS / 32) * NB + NB + NB + NB * NB + 4);
 }
 
+// Threads of a panel CTA: short panels and FP64 panels use fewer warps, because the
+// cross-warp reductions dominate there (an FP64 warp instruction is slow on this part).
+template <typename T>
+int panel_threads(int h) {
+  if (sizeof(T) == 8) return h > 1024 ? 256 : 128;
+  return h > 1024 ? 512 : (h > 256 ? 256 : 128);
+}
+
 // Reduce NV per-thread values over the whole CTA; result in out[0..NV).
 template <typename T, int NV, int NT>
 __device__ __forceinline__ void block_sum(T (&vals)[NV], T *red, T *out) {
@@ -61,8 +69,8 @@ __device__ __forceinline__ int panel_row(bool stacked, int c0, int d, int r) {
   return stacked ? (r < NB ? c0 + r : d + r - NB) : c0 + r;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H, int d, int c0, int stacked) {
+template <typename T, int PT>
+__global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, int c0, int stacked) {
   extern __shared__ __align__(16) uint8_t sm_raw[];
   const int64_t pslot = (int64_t)H * d;
   M += blockIdx.x * pslot;
@@ -72,7 +80,7 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
   const int hp = h | 1;
   T *Ps = reinterpret_cast<T *>(sm_raw);                  // NB x hp
   T *red = Ps + NB * hp;                                  // 16 warps x NB
-  T *sums = red + (PF_THREADS / 32) * NB;                 // NB
+  T *sums = red + (PT / 32) * NB;                 // NB
   T *wv = sums + NB;                                      // NB
   T *Ts = wv + NB;                                        // NB x NB
   T *scal = Ts + NB * NB;                                 // [tau, rdiag, head]
@@ -80,16 +88,16 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
   T *base = M + (int64_t)c0 * H;                          // column c0
 
   for (int c = 0; c < NB; ++c)
-    for (int r = tid; r < h; r += PF_THREADS)
+    for (int r = tid; r < h; r += PT)
       Ps[c * hp + r] = base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H];
-  for (int e = tid; e < NB * NB; e += PF_THREADS) Ts[e] = 0;
+  for (int e = tid; e < NB * NB; e += PT) Ts[e] = 0;
   __syncthreads();
 
   for (int jj = 0; jj < NB; ++jj) {
     T *x = Ps + jj * hp;
     T part[1] = {0};
-    for (int r = jj + 1 + tid; r < h; r += PF_THREADS) part[0] += x[r] * x[r];
-    block_sum<T, 1, PF_THREADS>(part, red, sums);
+    for (int r = jj + 1 + tid; r < h; r += PT) part[0] += x[r] * x[r];
+    block_sum<T, 1, PT>(part, red, sums);
     // every thread derives the reflector from the reduced norm (no broadcast round trip)
     const T alpha = x[jj];
     const T sig = sums[0];
@@ -106,20 +114,20 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
     T dots[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) dots[c] = 0;
-    for (int r = jj + 1 + tid; r < h; r += PF_THREADS) {
+    for (int r = jj + 1 + tid; r < h; r += PT) {
       T vr = x[r] * inv_head;
       x[r] = vr;
 #pragma unroll
       for (int c = 0; c < NB; ++c) dots[c] += (c == jj) ? T(0) : Ps[c * hp + r] * vr;
     }
-    block_sum<T, NB, PF_THREADS>(dots, red, sums);
+    block_sum<T, NB, PT>(dots, red, sums);
     if (tid < NB && tid != jj) wv[tid] = Ps[tid * hp + jj] + sums[tid];
     __syncthreads();
     if (tid == 0) x[jj] = rd;
     for (int c = jj + 1; c < NB; ++c) {
       T w = tau * wv[c];
       T *col = Ps + c * hp;
-      for (int r = jj + 1 + tid; r < h; r += PF_THREADS) col[r] -= w * x[r];
+      for (int r = jj + 1 + tid; r < h; r += PT) col[r] -= w * x[r];
       if (tid == 0) col[jj] -= w;
     }
     if (tid < jj) {
@@ -133,15 +141,15 @@ __global__ void __launch_bounds__(PF_THREADS) k_panel(T *M, T *Vx, T *Tm, int H,
   }
   for (int c = 0; c < NB; ++c) {
     T *vcol = Vx + (int64_t)(c0 + c) * H;
-    for (int r = tid; r < H; r += PF_THREADS) {
+    for (int r = tid; r < H; r += PT) {
       int lr;                                   // logical panel row of physical row r, or -1
       if (stacked) lr = (r >= c0 && r < c0 + NB) ? r - c0 : ((r >= d && r < d + c0 + NB) ? r - d + NB : -1);
       else lr = r - c0;
       vcol[r] = (lr < 0 || lr < c) ? T(0) : (lr == c ? T(1) : Ps[c * hp + lr]);
     }
-    for (int r = tid; r < h; r += PF_THREADS) base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H] = Ps[c * hp + r];
+    for (int r = tid; r < h; r += PT) base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H] = Ps[c * hp + r];
   }
-  for (int e = tid; e < NB * NB; e += PF_THREADS) {
+  for (int e = tid; e < NB * NB; e += PT) {
     int i = e / NB, j = e % NB;              // Ts is row-major [i][j]; Tm column-major
     Tm[(c0 + i) + (int64_t)(c0 + j) * d] = Ts[e];
   }
@@ -273,10 +281,20 @@ struct Stage {
 
 template <typename T>
 Error run_panel(const Stage<T> &s, int d, int c0, cudaStream_t st) {
-  size_t smem = panel_smem<T>(s.stacked ? c0 + 2 * NB : s.H - c0);
-  CK_CUDA(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int h = s.stacked ? c0 + 2 * NB : s.H - c0;
+  size_t smem = panel_smem<T>(h);
+  const int pt = panel_threads<T>(h);
   note_launch();
-  k_panel<T><<<s.P, PF_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0, s.stacked ? 1 : 0);
+  if (pt == 512) {
+    CK_CUDA(cudaFuncSetAttribute(k_panel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_panel<T, 512><<<s.P, 512, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0, s.stacked ? 1 : 0);
+  } else if (pt == 256) {
+    CK_CUDA(cudaFuncSetAttribute(k_panel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_panel<T, 256><<<s.P, 256, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0, s.stacked ? 1 : 0);
+  } else {
+    CK_CUDA(cudaFuncSetAttribute(k_panel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_panel<T, 128><<<s.P, 128, smem, st>>>(s.M, s.Vx, s.Tm, s.H, d, c0, s.stacked ? 1 : 0);
+  }
   CK_CUDA(cudaGetLastError());
   return ok();
 }
