@@ -119,6 +119,23 @@ ckinv_status ckinv_check(ckinv_ctx *ctx, ckinv_stream stream);
 ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed,
                          uint32_t *sign_bits, int32_t *cols, ckinv_stream stream);
 
+/* The same draw as ckinv_omega for callers that cannot allocate device memory (for
+ * example a program that reserves all device memory for its own pool up front, or code
+ * that must not take the implicit device synchronisation of an allocation).  The paper has
+ * no counterpart: this is an interface variant, not part of the method.
+ *   Runs on the calling thread's current device; needs no context; calls no allocator.
+ *   Its scratch is one fixed device array of about 304 KB per device (a 65536-bin key
+ *   histogram, room for 4096 candidate columns, counters), kept until the process exits.
+ *   The first call on a device resolves that array's device address (set-up).
+ *   Limits: 1 <= n <= 2^31, 1 <= d <= min(512, N); larger sizes return CKINV_EINVAL with a
+ *   message in ckinv_last_error(NULL).
+ *   Every call on a device shares the array: calls whose GPU work overlaps (other streams,
+ *   other host threads) race on it and must be serialised by the caller.
+ *   Outputs as in ckinv_omega (device, caller-owned).  The call synchronises `stream`
+ *   before returning, to report a candidate-list overflow as CKINV_EUNSUPPORTED. */
+ckinv_status ckinv_omega_noalloc(int64_t n, int32_t d, uint64_t seed, uint32_t *sign_bits,
+                                 int32_t *cols, ckinv_stream stream);
+
 /* Sketch Y = K0 Omega (Sec. 3.1-3.2; Sec. 3.3's K_hat), computed matrix-free from the
  * points: kernel tiles are evaluated on the fly and contracted with Omega.
  *   points: n x dim FP32 row-major (x_i at points[i*dim]); NULL for CKINV_DENSE.

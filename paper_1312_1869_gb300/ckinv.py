@@ -52,6 +52,7 @@ _SIGS = {
     "ckinv_last_error": (ctypes.c_char_p, [_VP]),
     "ckinv_check": (ctypes.c_int, [_VP, _VP]),
     "ckinv_omega": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
+    "ckinv_omega_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
     "ckinv_sketch": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                     ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "ckinv_sketch_dlogl": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
@@ -189,6 +190,18 @@ def omega(ctx, n, d, seed, stream=None):
     cols = torch.empty((d,), dtype=torch.int32, device="cuda")
     ctx._raise(load().ckinv_omega(ctx.handle, n, d, seed, _ptr(bits), _ptr(cols), _stream(stream)))
     return bits, cols
+
+
+def omega_noalloc(n, d, seed, sign_bits=None, cols=None, stream=None):
+    """The Omega draw without any library allocation (outputs are the caller's tensors)."""
+    if sign_bits is None:
+        sign_bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device="cuda")
+    if cols is None:
+        cols = torch.empty((d,), dtype=torch.int32, device="cuda")
+    st = load().ckinv_omega_noalloc(n, d, seed, _ptr(sign_bits), _ptr(cols), _stream(stream))
+    if st != OK:
+        raise CKInvError(st, load().ckinv_last_error(None).decode())
+    return sign_bits, cols
 
 
 def sketch(ctx, plan, kern, points=None, K=None, Y=None, stream=None):

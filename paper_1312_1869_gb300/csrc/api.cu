@@ -368,6 +368,8 @@ Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kerne
 
 }  // namespace
 
+void ckinv::set_static_error(const std::string &msg) { g_static_err = msg; }
+
 // ====================================================================== exported ABI
 extern "C" {
 

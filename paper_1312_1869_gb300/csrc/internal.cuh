@@ -35,6 +35,9 @@ struct Error {
 
 inline Error ok() { return Error{CKINV_OK, std::string()}; }
 
+// Message returned by ckinv_last_error(NULL) for calls that have no context.
+void set_static_error(const std::string &msg);
+
 // Host-side count of kernel launches issued by the library (diagnostics).
 unsigned long long &launch_counter();
 inline void note_launch() { __atomic_add_fetch(&launch_counter(), 1ull, __ATOMIC_RELAXED); }

@@ -219,3 +219,106 @@ Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st) {
 }
 
 }  // namespace ckinv
+
+// ===================================================================== no-allocation draw
+// A variant of the Omega draw for callers that cannot allocate device memory: programs
+// that hand all device memory to their own pool up front and leave nothing for the CUDA
+// allocator, and code that must not take the implicit device synchronisation an allocation
+// can cause.  Its scratch (the 65536-bin key histogram, the candidate list and a few
+// counters) is one file-scope device array, so the entry point needs no context and calls
+// no allocator.  The array exists once per device that loads the library and lives until
+// the process exits; every call on a device reuses it, so calls whose work overlaps on the
+// GPU (different streams, or different host threads) race on it and must be serialised by
+// the caller.
+namespace ckinv {
+namespace {
+
+constexpr size_t kNoAllocHistBytes = sizeof(uint32_t) * 65536;
+constexpr size_t kNoAllocSmallBytes = 256;   // counters and the error word
+constexpr size_t kNoAllocKeyBytes = sizeof(unsigned long long) * kSortCap;
+constexpr size_t kNoAllocIdxBytes = sizeof(uint32_t) * kSortCap;
+constexpr size_t kNoAllocBytes = kNoAllocHistBytes + kNoAllocSmallBytes + kNoAllocKeyBytes + kNoAllocIdxBytes;
+
+static __device__ __align__(256) unsigned char g_omega_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_scratch_addr[kMaxDevices] = {};
+int g_scratch_ready[kMaxDevices] = {};
+
+// Device address of this device's scratch array, resolved once per device with that device
+// current (the host-side symbol is only a stand-in, never a device address).
+Error scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  CK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(CKINV_EUNSUPPORTED, "device index above 63");
+  if (!__atomic_load_n(&g_scratch_ready[dev], __ATOMIC_ACQUIRE)) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_omega_scratch);
+    if (e != cudaSuccess)
+      return fail(CKINV_ECUDA, std::string("cudaGetSymbolAddress of the Omega scratch: ") + cudaGetErrorString(e));
+    g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+    __atomic_store_n(&g_scratch_ready[dev], 1, __ATOMIC_RELEASE);
+  }
+  *out = g_scratch_addr[dev];
+  return ok();
+}
+
+}  // namespace
+}  // namespace ckinv
+
+extern "C" ckinv_status ckinv_omega_noalloc(int64_t n, int32_t d, uint64_t seed, uint32_t *sign_bits, int32_t *cols,
+                                            ckinv_stream stream) {
+  using namespace ckinv;
+  if (!sign_bits || !cols) {
+    set_static_error("ckinv_omega_noalloc: null output pointer");
+    return CKINV_EINVAL;
+  }
+  if (n < 1 || n > ((int64_t)1 << 31) || d < 1 || d > 512 || (int64_t)d > padded_order(n)) {
+    set_static_error("ckinv_omega_noalloc: need 1 <= n <= 2^31 and 1 <= d <= min(512, N); its fixed scratch "
+                     "holds a 65536-bin histogram and 4096 candidates");
+    return CKINV_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char *base = nullptr;
+  {
+    Error e = scratch_for_current_device(&base);
+    if (e.st != CKINV_OK) {
+      set_static_error(e.msg);
+      return e.st;
+    }
+  }
+  uint32_t *hist = reinterpret_cast<uint32_t *>(base);
+  uint32_t *small = reinterpret_cast<uint32_t *>(base + kNoAllocHistBytes);
+  int *err = reinterpret_cast<int *>(small + 32);
+  unsigned long long *cand = reinterpret_cast<unsigned long long *>(base + kNoAllocHistBytes + kNoAllocSmallBytes);
+  uint32_t *cand_idx = reinterpret_cast<uint32_t *>(base + kNoAllocHistBytes + kNoAllocSmallBytes + kNoAllocKeyBytes);
+  const int64_t N = padded_order(n);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  // the array keeps the previous call's contents: clear what must start at zero
+  if (cudaMemsetAsync(base, 0, kNoAllocHistBytes + kNoAllocSmallBytes, st) != cudaSuccess) return CKINV_ECUDA;
+  note_launch();
+  k_signs<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, k0, k1, sign_bits);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CKINV_ECUDA;
+  const int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)sms * 8);
+  note_launch();
+  k_key_hist<<<grid, 256, 0, st>>>(N, k0, k1, hist);
+  note_launch();
+  k_pick_bin<<<1, 1024, 0, st>>>(hist, d, small);
+  note_launch();
+  k_collect<<<grid, 256, 0, st>>>(N, k0, k1, small, cand, cand_idx, (uint32_t)kSortCap, small + 2);
+  note_launch();
+  k_finalize<<<1, 1024, 0, st>>>(cand, cand_idx, small + 2, d, cols, err);
+  if (cudaGetLastError() != cudaSuccess) return CKINV_ECUDA;
+  // report a candidate-list overflow (not expected below n = 2^24) before returning
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return CKINV_ECUDA;
+  if (herr) {
+    set_static_error("ckinv_omega_noalloc: more than 4096 candidate columns share the selection bin");
+    return CKINV_EUNSUPPORTED;
+  }
+  return CKINV_OK;
+}
