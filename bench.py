@@ -38,6 +38,9 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
+KERNEL_NAMES = {0: "squared-exponential", 1: "matern-5/2"}
+
+
 def workload_config(name):
     cfg = dict(synth.CONFIGS[name])
     cfg["workload"] = name
@@ -148,7 +151,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": cfg["workload"], "n": cfg["n"], "d": cfg["d"], "m": cfg["m"],
-                       "kernel": "squared-exponential", "lengthscale": cfg["ell"], "nugget": cfg["tau"]},
+                       "kernel": KERNEL_NAMES[cfg["kind"]], "lengthscale": cfg["ell"], "nugget": cfg["tau"]},
             "cpu_baseline": {"value": sps, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": "FP64 oracle sketch of rows 0..%d of %d per step (Omega built in the "
                                        "step), extrapolated to all rows; QR and solve not included"
@@ -292,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                 "config": {"workload": cfg["workload"], "n": n, "d": d, "m": m, "dim": dim,
-                           "kernel": "squared-exponential", "lengthscale": cfg["ell"], "nugget": cfg["tau"],
+                           "kernel": KERNEL_NAMES[cfg["kind"]], "lengthscale": cfg["ell"], "nugget": cfg["tau"],
                            "block_rows": cfg["block_rows"], "refine_steps": args.refine,
                            "tree_fp64_levels": args.fp64_levels, "parallelism": "replicas" if world > 1 else "1gpu",
                            "l2": "flushed between steps (256 MB write); Y and Q_hat (537 MB each) exceed L2"},

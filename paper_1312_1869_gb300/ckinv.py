@@ -293,10 +293,13 @@ def kinv_a(ctx, plan, kern, points, A, X=None, stream=None):
     m = 1 if A.dim() == 1 else A.shape[1]
     if A.dim() == 2 and A.stride(0) != 1:
         raise ValueError("A must be column-major")
-    lda = n if A.dim() == 1 else A.stride(1)
+    # a single column may carry any stride along its (size-1) second dimension
+    lda = n if (A.dim() == 1 or m == 1) else A.stride(1)
     if X is None:
         X = torch.empty((m, n), dtype=torch.float32, device=A.device).t()
-    ldx = n if X.dim() == 1 else X.stride(1)
+    if X.dim() == 2 and X.stride(0) != 1:
+        raise ValueError("X must be column-major")
+    ldx = n if (X.dim() == 1 or m == 1) else X.stride(1)
     pd, kd = plan.desc(), kern.desc()
     ctx._raise(load().ckinv_kinv_a(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(points), _ptr(A), lda, m,
                                    _ptr(X), ldx, _stream(stream)))

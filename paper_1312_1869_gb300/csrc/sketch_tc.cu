@@ -1,13 +1,15 @@
 // Fused sketch Y = K0 Omega (Sec. 3.1-3.3) on the 5th-generation tensor cores.
 //
 // One CTA owns 128 rows of Y and all d <= 512 columns; the FP32 accumulator lives in
-// TMEM (128 lanes x d columns).  The contraction runs over the n points in blocks of 64:
-//   * warps 2..9 evaluate the 128 x 64 kernel tile in FP32 (exp2 on the MUFU), split it
-//     into 1-3 BF16 terms and store them straight into the 128B-swizzled K-major SMEM
+// TMEM (128 lanes x d columns).  The contraction runs over the n points in blocks of 32:
+//   * warps 2..9 evaluate the 128 x 32 kernel tile in FP32 (exp2 on the MUFU), split it
+//     into 1-3 BF16 terms and store them straight into the 64B-swizzled K-major SMEM
 //     layout the MMA reads (no HBM traffic for K0 at all);
-//   * warp 0 streams the 64 x d tile of the +-1 Omega pattern (BF16, exact) by TMA;
+//   * warp 0 streams the 32 x d tile of the +-1 Omega pattern (BF16, exact) by TMA;
 //   * warp 1 issues tcgen05.mma (M = 128, N = min(d, 256) per instruction, K = 16) and
-//     commits each stage back to the producers through mbarriers;
+//     commits each stage back to the producers through mbarriers.  Short blocks keep a
+//     stage small (40 KB at d = 512), so that 3-8 stages are in flight and the tensor
+//     pipe does not wait on the producer/consumer round trip;
 //   * after the last block, warps 2..9 read TMEM with tcgen05.ld, scale by variance * c
 //     and write Y (coalesced along rows: Y is column-major).
 // Every mbarrier wait is bounded; on timeout the CTA records DERR_TIMEOUT, drains its
@@ -22,10 +24,16 @@ namespace ckinv {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;
-constexpr int kThreads = 320;          // 10 warps
-constexpr int kProducerThreads = 256;  // warps 2..9
+constexpr int BK = 64;                  // points per pipeline stage
+constexpr uint32_t kRowBytes = BK * 2;  // one K-major row of a BF16 tile: 128 B, 128B-swizzled
+constexpr int kProducerWarps = 8;       // warps 2 .. 9
+constexpr int kRowsPerLane = 1;         // tile rows per producer lane
+constexpr int kPtSlots = 12;            // shared-memory slots of raw block coordinates (>= stages + 4)
+constexpr uint32_t kPtSlotBytes = BK * 3 * 4;   // one block of up to 3-D points
+constexpr int kKParts = kProducerWarps / 4;   // epilogue warps sharing one 32-row TMEM quadrant
+constexpr int kThreads = 64 + 32 * kProducerWarps;
 constexpr uint32_t kATileBytes = BM * BK * 2;  // 16 KB per BF16 term
+static_assert(kProducerWarps % 4 == 0, "epilogue split");
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -56,17 +64,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with cluster-scope acquire, for barriers that threads of the peer CTA arrive on.
+__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 // Bounded wait: gives up after ~1 s or when another warp has flagged an abort.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                       bool cluster_scope = false) {
+  auto poll = [&]() { return cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); };
+  if (poll()) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (poll()) return true;
     if ((it & 15u) == 15u) {
       if (*abort_flag) return false;
       if (global_ns() - t0 > 1000000000ull) {
@@ -77,13 +98,32 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
   }
 }
 
-// Warp-uniform bounded wait: lane 0 polls, the warp agrees on the outcome.
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  return ok != 0;
+// Warp-wide bounded wait: every lane polls, so that each lane acquires the phase itself (no
+// __syncwarp, whose memory ordering costs ~200 clocks), and the warp leaves together.
+__device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if ((it & 15u) == 15u) {
+      int stop = 0;
+      if ((threadIdx.x & 31) == 0) {
+        if (*abort_flag) stop = 1;
+        else if (global_ns() - t0 > 1000000000ull) {
+          *abort_flag = 1;
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+    }
+  }
+}
+// Contiguous bulk copy global -> shared (async proxy), completion counted on an mbarrier;
+// both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -95,22 +135,46 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       "l"(map), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
+// Arrive on the mbarrier at this offset in each CTA of the pair named by ctaMask once all
+// prior MMAs of the pair are done.
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accum) {
+// D[256 x N] (+)= A[256 x 16] B[16 x N] over the CTA pair: A rows 0-127 and B columns
+// 0 .. N/2-1 from this CTA's shared memory, the rest from the peer's at the same offsets;
+// D rows 0-127 in this CTA's TMEM, 128-255 in the peer's.
+__device__ __forceinline__ void tc_mma_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+// Shared::cluster address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   uint32_t r[8];
@@ -124,19 +188,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// SMEM matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// SMEM matrix descriptor: K-major rows of kRowBytes, swizzled by the matching mode,
+// 8-row groups 8 * kRowBytes apart.
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+  constexpr uint64_t layout = (kRowBytes == 128) ? 2 : (kRowBytes == 64 ? 4 : 6);   // 128B / 64B / 32B
   uint64_t desc = 0;
   desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
   desc |= (uint64_t)1 << 16;                          // leading byte offset (unused)
-  desc |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  desc |= (uint64_t)((8 * kRowBytes) >> 4) << 32;     // stride byte offset
   desc |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
-  desc |= (uint64_t)2 << 61;                          // swizzle: 128B
+  desc |= layout << 61;                               // swizzle mode
   return desc;
 }
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128.
+// Physical 16-byte chunk of logical chunk c in row r under that swizzle.
+__device__ __forceinline__ uint32_t swz_chunk(uint32_t c, uint32_t r) {
+  return (kRowBytes == 128) ? (c ^ (r & 7u)) : (kRowBytes == 64 ? (c ^ ((r >> 1) & 3u)) : (c ^ ((r >> 2) & 1u)));
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 256 (pair).
 __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
 }
 
 struct TcArgs {
@@ -144,10 +214,11 @@ struct TcArgs {
   int64_t m;       // output rows (dense mode: rows of A)
   int dim;
   int d;
-  int num_kb;      // 64-point blocks in total
+  int num_kb;      // BK-point blocks in total
   int kb_per_cta;  // blocks per CTA along the contraction (split over gridDim.y)
   int stages;
-  int box_rows;    // rows of Omega^T per TMA box
+  int n0, n1;      // N of the first and second MMA column chunk (n1 = 0: a single chunk)
+  int box_rows;    // rows of Omega^T per TMA box (divides n0 / 2 and n1 / 2)
   KernelParams kp;
   const float *pts;
   const float *A;  // dense mode: row i of A at A + i * lda (K-major)
@@ -160,7 +231,9 @@ struct TcArgs {
 };
 
 // MODE 0: A = kernel tile evaluated from the points;  MODE 1: A = a dense FP32 matrix.
-template <int NSPLIT, bool DERIV, int MODE>
+// KIND is the covariance function of MODE 0 (fixed at compile time so that the inner
+// loop carries no branch).
+template <int NSPLIT, bool DERIV, int MODE, int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_tc(const __grid_constant__ CUtensorMap tmapB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -168,20 +241,32 @@ __global__ void __launch_bounds__(kThreads, 1)
   // 1024-aligned stage tiles
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   const int S = a.stages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 26);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 34 + kPtSlots);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  float4 *xs_all = reinterpret_cast<float4 *>(smem_raw + 512);   // 8 warps x 32 points
+  const float *pt_slots = reinterpret_cast<const float *>(smem_raw + 512);   // kPtSlots blocks of raw points
   uintptr_t tiles_u =
-      (reinterpret_cast<uintptr_t>(smem_raw) + 512 + 8 * 32 * 16 + 1023) & ~(uintptr_t)1023;
+      (reinterpret_cast<uintptr_t>(smem_raw) + 512 + kPtSlots * kPtSlotBytes + 1023) & ~(uintptr_t)1023;
   uint8_t *tiles = reinterpret_cast<uint8_t *>(tiles_u);
-  const uint32_t b_bytes = (uint32_t)a.d * BK * 2;
+  // this CTA's half of the Omega tile: n0/2 rows of chunk 0, then n1/2 rows of chunk 1
+  const uint32_t b_bytes = (uint32_t)(a.n0 + a.n1) / 2 * kRowBytes;
   const uint32_t stage_bytes = NSPLIT * kATileBytes + b_bytes;
+  const uint32_t b1_off = (uint32_t)(a.n0 / 2) * kRowBytes;
+  const uint32_t rank = cluster_rank();       // 0: the CTA that issues the pair's MMAs
 
+  // fullA: this CTA's A tiles are written (one arrival per producer thread);
+  // fullB: this CTA's Omega half has landed;
+  // peerB (rank 0): the peer's A tiles and Omega half are ready (one cluster-scope arrival
+  //   from the peer, made by a thread that does nothing else);
+  // empty: the pair's MMAs are done with the stage (committed to both CTAs).
   auto fullA = [&](int s) { return smem_u32(bars + s); };
   auto fullB = [&](int s) { return smem_u32(bars + 8 + s); };
   auto empty = [&](int s) { return smem_u32(bars + 16 + s); };
-  const uint32_t accum_bar = smem_u32(bars + 24);
-  const uint32_t drain_bar = smem_u32(bars + 25);
+  auto peerB = [&](int s) { return smem_u32(bars + 24 + s); };
+  const uint32_t accum_bar = smem_u32(bars + 32);
+  const uint32_t drain_bar = smem_u32(bars + 33);
+  // fullP(j): the raw coordinates of the block in point slot j have landed
+  auto fullP = [&](int j) { return smem_u32(bars + 34 + j); };
+  auto pt_slot = [&](int j) { return smem_u32(pt_slots) + (uint32_t)j * kPtSlotBytes; };
   auto a_tile = [&](int s, int t) {
     return smem_u32(tiles + (size_t)s * stage_bytes + (size_t)t * kATileBytes);
   };
@@ -196,59 +281,91 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(fullA(s), kProducerThreads / 32);
+      mbar_init(fullA(s), 32 * kProducerWarps);
       mbar_init(fullB(s), 1);
       mbar_init(empty(s), 1);
+      mbar_init(peerB(s), 1);
     }
+    for (int j = 0; j < kPtSlots; ++j) mbar_init(fullP(j), 1);
     mbar_init(accum_bar, 1);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    // collective over the pair: one warp of each CTA, the same columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync_all();   // every barrier of the cluster is initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer (Omega)
     if (lane == 0) {
-      int issued = 0;
+      // Points: the raw coordinates of block kb go to slot kb % kPtSlots, L = kPtSlots - S
+      // blocks ahead of the stage being fetched. The slot's previous block (kb - S) was read
+      // by the producers before they released its stage, which the empty wait below
+      // observes, so the slot is free when the copy is issued.
+      const int L = kPtSlots - S;
+      auto issue_points = [&](int kb) {
+        if (MODE != 0 || kb >= nkb) return;
+        const int j = kb % kPtSlots;
+        const int64_t k0 = (int64_t)(kb_begin + kb) * BK;
+        if (k0 + BK <= a.n) {
+          const uint32_t bytes = (uint32_t)(BK * a.dim * 4);
+          mbar_arrive_expect_tx(fullP(j), bytes);
+          bulk_load(pt_slot(j), a.pts + k0 * a.dim, bytes, fullP(j));
+        } else {
+          mbar_arrive(fullP(j));     // the last, partial block: producers read global memory
+        }
+      };
+      for (int kb = 0; kb < L; ++kb) issue_points(kb);
+      // this CTA fetches its half of each column chunk: rows c n0 + rank n_c/2 + [0, n_c/2)
+      int issued = 0, pts_issued = L;
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+        issue_points(kb + L);
+        pts_issued = kb + L + 1;
         mbar_arrive_expect_tx(fullB(s), b_bytes);
         const int kx = (kb_begin + kb) * BK;
-        tma_load_2d(b_tile(s), &tmapB, fullB(s), kx, 0);
-        if (a.box_rows < a.d)
-          tma_load_2d(b_tile(s) + (uint32_t)a.box_rows * 128u, &tmapB, fullB(s), kx, a.box_rows);
+        const int h0 = a.n0 / 2, h1 = a.n1 / 2;
+        for (int o = 0; o < h0; o += a.box_rows)
+          tma_load_2d(b_tile(s) + (uint32_t)o * kRowBytes, &tmapB, fullB(s), kx, (int)rank * h0 + o);
+        for (int o = 0; o < h1; o += a.box_rows)
+          tma_load_2d(b_tile(s) + b1_off + (uint32_t)o * kRowBytes, &tmapB, fullB(s), kx, a.n0 + (int)rank * h1 + o);
         ++issued;
       }
-      // every copy this CTA issued must land before its shared memory is released
+      // every copy this CTA issued must land before shared memory is released
       volatile int never = 0;
       int first = issued - S < 0 ? 0 : issued - S;
       for (int kb = first; kb < issued; ++kb)
         mbar_wait(fullB(kb % S), (uint32_t)(kb / S) & 1u, &never);
+      if (MODE == 0) {
+        const int last = min(pts_issued, nkb);
+        for (int kb = max(0, last - kPtSlots); kb < last; ++kb)
+          mbar_wait(fullP(kb % kPtSlots), (uint32_t)(kb / kPtSlots) & 1u, &never);
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      const uint32_t id0 = idesc_bf16(a.d < 256 ? a.d : 256);
-      const uint32_t id1 = idesc_bf16(a.d > 256 ? a.d - 256 : 16);
+    // ------------------------------------------------------------ MMA issuer (rank 0)
+    if (lane == 0 && rank == 0) {
+      const uint32_t id0 = idesc_bf16(a.n0);
+      const uint32_t id1 = idesc_bf16(a.n1 > 0 ? a.n1 : 16);
       bool good = true;
       int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag)) {
+        if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag) ||
+            !mbar_wait(peerB(s), ph, abort_flag, true)) {
           good = false;
           break;
         }
@@ -257,146 +374,180 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < NSPLIT; ++t) {
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            uint64_t ad = sw128_desc(a_tile(s, t) + kk * 32);
-            uint64_t bd = sw128_desc(b_tile(s) + kk * 32);
+            uint64_t ad = sw_desc(a_tile(s, t) + kk * 32);
+            uint64_t bd = sw_desc(b_tile(s) + kk * 32);
             uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
-            tc_mma(tmem_base, ad, bd, id0, acc);
-            if (a.d > 256) {
-              uint64_t bd1 = sw128_desc(b_tile(s) + 256u * 128u + kk * 32);
-              tc_mma(tmem_base + 256u, ad, bd1, id1, acc);
+            tc_mma_pair(tmem_base, ad, bd, id0, acc);
+            if (a.n1 > 0) {
+              uint64_t bd1 = sw_desc(b_tile(s) + b1_off + kk * 32);
+              tc_mma_pair(tmem_base + (uint32_t)a.n0, ad, bd1, id1, acc);
             }
           }
         }
-        tc_commit(empty(s));
+        tc_commit_pair(empty(s), 0x3);
         ++issued;
       }
-      if (good) tc_commit(accum_bar);
+      if (good) tc_commit_pair(accum_bar, 0x3);
       if (issued > 0) {
-        // all MMAs of this CTA must finish before TMEM is released
+        // all MMAs of the pair must finish before either CTA releases TMEM or shared memory
         volatile int never = 0;
-        tc_commit(drain_bar);
+        tc_commit_pair(drain_bar, 0x1);
         mbar_wait(drain_bar, 0u, &never);
+      }
+    } else if (lane == 0) {
+      // rank 1: tell the MMA issuer when this CTA's A tiles and Omega half of each stage are
+      // ready (acquire here, release at cluster scope to rank 0)
+      const uint32_t peer_bar0 = map_to_rank(peerB(0), 0);
+      for (int kb = 0; kb < nkb; ++kb) {
+        int s = kb % S;
+        uint32_t ph = (uint32_t)(kb / S) & 1u;
+        if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag)) break;
+        mbar_arrive_remote(peer_bar0 + 8u * (uint32_t)s);
       }
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ A-tile producers
-    // producer warp pw = warp - 2 handles tile rows 32 (pw % 4) .. +31 and the k-half
-    // pw / 4 of every 64-point block; each lane owns one row.
+    // Lane l of producer warp pw owns the kRowsPerLane tile rows l + 32 j (+ the warp's row
+    // group) and, of every block, the KH points of k-part h: each staged point is read
+    // once from shared memory and used for kRowsPerLane kernel entries.
+    constexpr int RG = BM / (32 * kRowsPerLane);   // row groups
+    constexpr int KP = kProducerWarps / RG;        // k-parts
+    constexpr int KH = BK / KP;                    // points per k-part
+    constexpr int CH = KH / 8;                     // 16-byte chunks per k-part and row
+    static_assert(RG * KP == kProducerWarps && KH % 8 == 0 && KH <= 32, "producer layout");
     const int pw = warp - 2;
-    const int r = (pw & 3) * 32 + lane;
-    const int h = pw >> 2;
-    float4 *xw = xs_all + pw * 32;
-    const int64_t irow = min(i0 + r, (MODE == 0 ? a.n : a.m) - 1);
+    const int g = pw % RG, h = pw / RG;
+    const int64_t rows_total = (MODE == 0) ? a.n : a.m;
     const float cs = a.kp.coord_scale;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-    if (MODE == 0) {
-      x0 = a.pts[irow * a.dim] * cs;
-      if (a.dim > 1) x1 = a.pts[irow * a.dim + 1] * cs;
-      if (a.dim > 2) x2 = a.pts[irow * a.dim + 2] * cs;
-    }
-    const float *arow = (MODE == 1) ? a.A + irow * a.lda : nullptr;
-    const bool row_ok = (MODE == 1) ? (i0 + r < a.m) : true;
-    const int kind = a.kp.kind;
     const float inv_l = a.kp.inv_l;
-    const uint32_t rowbase = (uint32_t)r * 128u;
-    const uint32_t swz = (uint32_t)(r & 7);
-    bool good = true;
-    // the point this lane stages for the next block, fetched one block ahead
-    auto load_point = [&](int kb) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      int64_t k = (int64_t)(kb_begin + kb) * BK + h * 32 + lane;
-      if (MODE == 0 && kb < nkb && k < a.n) {
-        v.x = a.pts[k * a.dim] * cs;
-        if (a.dim > 1) v.y = a.pts[k * a.dim + 1] * cs;
-        if (a.dim > 2) v.z = a.pts[k * a.dim + 2] * cs;
-        v.w = 1.0f;                        // marks a real point
+    float xr[kRowsPerLane][3];
+    const float *arow[kRowsPerLane];
+    bool rok[kRowsPerLane];
+#pragma unroll
+    for (int j = 0; j < kRowsPerLane; ++j) {
+      const int r = g * 32 * kRowsPerLane + j * 32 + lane;
+      const int64_t irow = min(i0 + r, rows_total - 1);
+      xr[j][0] = xr[j][1] = xr[j][2] = 0.f;
+      if (MODE == 0) {
+        xr[j][0] = a.pts[irow * a.dim] * cs;
+        if (a.dim > 1) xr[j][1] = a.pts[irow * a.dim + 1] * cs;
+        if (a.dim > 2) xr[j][2] = a.pts[irow * a.dim + 2] * cs;
       }
-      return v;
-    };
-    float4 pnext = load_point(0);
-    for (int kb = 0; kb < nkb; ++kb) {
+      arow[j] = (MODE == 1) ? a.A + irow * a.lda : nullptr;
+      rok[j] = (i0 + r < rows_total);
+    }
+    // rows l + 32 j share l mod 8, hence the swizzle of their 16-byte chunks
+    const uint32_t lane_base = (uint32_t)(g * 32 * kRowsPerLane + lane) * kRowBytes;
+    bool good = true;
+    // one block: wait for its points and for the stage, fill the stage's A tiles
+    auto produce = [&](int kb) -> bool {
       int s = kb % S;
       uint32_t ph = (uint32_t)(kb / S) & 1u;
-      const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * 32;
-      const bool full_block = (kbase + 32 <= (MODE == 0 ? a.n : a.n));
-      if (MODE == 0) {
-        __syncwarp();                      // previous block's reads of xw are done
-        xw[lane] = pnext;
-        __syncwarp();
-        pnext = load_point(kb + 1);
-      }
-      if (!mbar_wait_warp(empty(s), ph ^ 1u, abort_flag)) { good = false; break; }
+      const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * KH;
+      const bool full_block = ((int64_t)(kb_begin + kb) * BK + BK <= a.n);
+      const int j = kb % kPtSlots;
+      if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag)) return false;
+      if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag)) return false;
+      const float *ps = pt_slots + (size_t)j * (kPtSlotBytes / 4) + (size_t)h * KH * a.dim;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float kv[8];
+      for (int c = 0; c < CH; ++c) {
+        float kv[kRowsPerLane][8];
         if (MODE == 0) {
-          if (full_block && a.dim <= 2) {
+          // differences in scaled coordinates: x cs - p cs, with p raw and x pre-scaled
+          if (full_block && a.dim == 2) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              float4 p = xw[c * 8 + u];
-              float dx = x0 - p.x, dy = x1 - p.y;
-              kv[u] = dev::kernel_value(kind, fmaf(dy, dy, dx * dx), inv_l, DERIV);
+              const float2 p = *reinterpret_cast<const float2 *>(ps + (c * 8 + u) * 2);
+#pragma unroll
+              for (int r = 0; r < kRowsPerLane; ++r) {
+                float dx = fmaf(-cs, p.x, xr[r][0]), dy = fmaf(-cs, p.y, xr[r][1]);
+                kv[r][u] = dev::kernel_value(KIND, fmaf(dy, dy, dx * dx), inv_l, DERIV);
+              }
+            }
+          } else if (full_block) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float *q = ps + (c * 8 + u) * a.dim;
+              const float px = q[0], py = a.dim > 1 ? q[1] : 0.f, pz = a.dim > 2 ? q[2] : 0.f;
+#pragma unroll
+              for (int r = 0; r < kRowsPerLane; ++r) {
+                float dx = fmaf(-cs, px, xr[r][0]), dy = fmaf(-cs, py, xr[r][1]), dz = fmaf(-cs, pz, xr[r][2]);
+                kv[r][u] = dev::kernel_value(KIND, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), inv_l, DERIV);
+              }
             }
           } else {
+            // the last, partial block: points straight from global memory, zero past n
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              float4 p = xw[c * 8 + u];
-              float dx = x0 - p.x, dy = x1 - p.y, dz = x2 - p.z;
-              float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              float v = dev::kernel_value(kind, r2, inv_l, DERIV);
-              kv[u] = (p.w != 0.0f) ? v : 0.0f;
+              const int64_t k = kbase + c * 8 + u;
+              const bool valid = k < a.n;
+              const float *q = a.pts + (valid ? k : 0) * a.dim;
+              const float px = q[0], py = a.dim > 1 ? q[1] : 0.f, pz = a.dim > 2 ? q[2] : 0.f;
+#pragma unroll
+              for (int r = 0; r < kRowsPerLane; ++r) {
+                float dx = fmaf(-cs, px, xr[r][0]), dy = fmaf(-cs, py, xr[r][1]), dz = fmaf(-cs, pz, xr[r][2]);
+                float v = dev::kernel_value(KIND, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), inv_l, DERIV);
+                kv[r][u] = valid ? v : 0.0f;
+              }
             }
           }
         } else {
           const int64_t k0 = kbase + c * 8;
-          if (row_ok && k0 + 8 <= a.n) {
-            float4 lo = *reinterpret_cast<const float4 *>(arow + k0);
-            float4 hi = *reinterpret_cast<const float4 *>(arow + k0 + 4);
-            kv[0] = lo.x; kv[1] = lo.y; kv[2] = lo.z; kv[3] = lo.w;
-            kv[4] = hi.x; kv[5] = hi.y; kv[6] = hi.z; kv[7] = hi.w;
-          } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) kv[u] = (row_ok && k0 + u < a.n) ? arow[k0 + u] : 0.0f;
-          }
-        }
-        const uint32_t chunk = (uint32_t)(h * 4 + c);
-        const uint32_t off = rowbase + ((chunk ^ swz) << 4);
+          for (int j = 0; j < kRowsPerLane; ++j) {
+            if (rok[j] && k0 + 8 <= a.n) {
+              float4 lo = *reinterpret_cast<const float4 *>(arow[j] + k0);
+              float4 hi = *reinterpret_cast<const float4 *>(arow[j] + k0 + 4);
+              kv[j][0] = lo.x; kv[j][1] = lo.y; kv[j][2] = lo.z; kv[j][3] = lo.w;
+              kv[j][4] = hi.x; kv[j][5] = hi.y; kv[j][6] = hi.z; kv[j][7] = hi.w;
+            } else {
 #pragma unroll
-        for (int t = 0; t < NSPLIT; ++t) {
-          uint32_t w[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(kv[2 * u], kv[2 * u + 1]);
-            w[u] = *reinterpret_cast<uint32_t *>(&b2);
-            if (t + 1 < NSPLIT) {
-              float2 back = __bfloat1622float2(b2);
-              kv[2 * u] -= back.x;
-              kv[2 * u + 1] -= back.y;
+              for (int u = 0; u < 8; ++u) kv[j][u] = (rok[j] && k0 + u < a.n) ? arow[j][k0 + u] : 0.0f;
             }
           }
-          const uint32_t dst = a_tile(s, t) + off;
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]),
-                       "r"(w[2]), "r"(w[3])
-                       : "memory");
+        }
+        const uint32_t off = lane_base + (swz_chunk((uint32_t)(h * CH + c), (uint32_t)lane) << 4);
+#pragma unroll
+        for (int j = 0; j < kRowsPerLane; ++j) {
+#pragma unroll
+          for (int t = 0; t < NSPLIT; ++t) {
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              __nv_bfloat162 b2 = __floats2bfloat162_rn(kv[j][2 * u], kv[j][2 * u + 1]);
+              w[u] = *reinterpret_cast<uint32_t *>(&b2);
+              if (t + 1 < NSPLIT) {
+                float2 back = __bfloat1622float2(b2);
+                kv[j][2 * u] -= back.x;
+                kv[j][2 * u + 1] -= back.y;
+              }
+            }
+            const uint32_t dst = a_tile(s, t) + off + (uint32_t)(j * 32) * kRowBytes;
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]),
+                         "r"(w[2]), "r"(w[3])
+                         : "memory");
+          }
         }
       }
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(fullA(s));
+      fence_async_smem();                  // this thread's tile writes -> visible to the tensor core
+      mbar_arrive(fullA(s));
+      return true;
+    };
+    for (int kb = 0; kb < nkb; ++kb) {
+      if (!produce(kb)) { good = false; break; }
     }
     // ------------------------------------------------------------ epilogue
-    bool e_ok = good && nkb > 0 && mbar_wait_warp(accum_bar, 0u, abort_flag);
+    bool e_ok = good && nkb > 0 && mbar_wait_lanes(accum_bar, 0u, abort_flag);
     if (e_ok) {
       tc_fence_after();
       const int q = warp & 3;                 // TMEM lane quadrant this warp may access
-      const int half = pw >> 2;               // two warps per quadrant split the columns
-      const int cols_half = a.d / 2;
+      const int part = pw >> 2;               // kKParts warps per quadrant split the columns
       const int64_t i = i0 + q * 32 + lane;
       const float scale = (float)a.kp.scale;
       const int64_t mrows = (MODE == 0) ? a.n : a.m;
       float *pout = a.part ? a.part + (int64_t)blockIdx.y * a.ldp * a.d : nullptr;
-      for (int j = half * cols_half; j < (half + 1) * cols_half; j += 8) {
+      for (int j = part * 8; j < a.d; j += 8 * kKParts) {
         float v[8];
         tmem_ld8(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)j, v);
         if (i < mrows) {
@@ -412,11 +563,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   tc_fence_before();
-  __syncthreads();
+  // no peer may still multicast into, or arrive on, this CTA's shared memory after it exits
+  cluster_sync_all();
   if (*abort_flag && threadIdx.x == 0) atomicOr(a.err, DERR_TIMEOUT);
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(tmem_cols));
   }
 }
@@ -434,13 +586,25 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-template <int NSPLIT, bool DERIV, int MODE>
+template <int NSPLIT, bool DERIV, int MODE, int KIND>
 Error launch(const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid, cudaStream_t st) {
-  auto kfn = k_sketch_tc<NSPLIT, DERIV, MODE>;
+  auto kfn = k_sketch_tc<NSPLIT, DERIV, MODE, KIND>;
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  grid.x = (unsigned)(ceil_div((int64_t)grid.x, 2) * 2);   // whole pairs; an extra CTA stores nothing
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   ::ckinv::note_launch();
-  kfn<<<grid, kThreads, smem, st>>>(map, a);
-  CK_CUDA(cudaGetLastError());
+  CK_CUDA(cudaLaunchKernelEx(&cfg, kfn, map, a));
   return ok();
 }
 
@@ -451,13 +615,24 @@ Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, si
   const OmegaCache &om = ctx->om;
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return fail(CKINV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
-  const int box_rows = d <= 256 ? d : d / 2;
+  // MMA column chunks: N = d for d <= 256, else two chunks (equal when d % 32 == 0) of
+  // N <= 256; each CTA of the pair holds N/2 rows of each chunk (a multiple of 8, so every
+  // half starts on a 1024-byte swizzle atom)
+  const int n0 = d <= 256 ? d : (d % 32 == 0 ? d / 2 : 256);
+  const int n1 = d - n0;
+  int box_rows = n0 / 2;
+  if (n1 > 0) {
+    int x = n0 / 2, y = n1 / 2;
+    while (y) { int t = x % y; x = y; y = t; }
+    box_rows = x;
+  }
   cuuint64_t gdim[2] = {(cuuint64_t)om.kpad, (cuuint64_t)d};
   cuuint64_t gstride[1] = {(cuuint64_t)om.kpad * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)om.omegaT, gdim, gstride, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, (kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B),
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(CKINV_ECUDA, "cuTensorMapEncodeTiled failed");
   memset(a, 0, sizeof(*a));
@@ -465,30 +640,44 @@ Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, si
   a->num_kb = (int)(om.kpad / BK);
   a->kb_per_cta = a->num_kb;
   a->box_rows = box_rows;
+  a->n0 = n0;
+  a->n1 = n1;
   a->err = ctx->d_err;
-  const size_t stage_bytes = (size_t)nsplit * kATileBytes + (size_t)d * BK * 2;
-  const size_t head = 512 + 8 * 32 * 16 + 1024;   // barriers, point buffers, alignment slack
+  const size_t stage_bytes = (size_t)nsplit * kATileBytes + (size_t)d / 2 * kRowBytes;
+  const size_t head = 512 + kPtSlots * kPtSlotBytes + 1024;   // barriers, point slots, alignment slack
   const size_t limit = 227 * 1024;
   int S = (int)((limit - head) / stage_bytes);
-  if (S > 4) S = 4;
-  if (S < 1) return fail(CKINV_EUNSUPPORTED, "sketch_tc: stage does not fit in shared memory");
+  if (S > 8) S = 8;   // also keeps kPtSlots - S >= 4 blocks of point prefetch
+  if (S < 1) return fail(CKINV_EUNSUPPORTED, "sketch_tc: a stage does not fit in shared memory");
   a->stages = S;
   *smem = head + (size_t)S * stage_bytes;
+  // A CTA with d > 256 holds all 512 TMEM columns; never let two of them share an SM (the
+  // second would block in tcgen05.alloc until the first exits).
+  if (d > 256) *smem = std::max(*smem, (size_t)(120 * 1024));
   return ok();
 }
 
-template <int MODE>
-Error dispatch(int nsplit, bool deriv, const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid,
-               cudaStream_t st) {
+template <int KIND>
+Error dispatch_kernel(int nsplit, bool deriv, const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid,
+                      cudaStream_t st) {
   switch (nsplit * 2 + (deriv ? 1 : 0)) {
-    case 2: return launch<1, false, MODE>(map, a, smem, grid, st);
-    case 3: return launch<1, true, MODE>(map, a, smem, grid, st);
-    case 4: return launch<2, false, MODE>(map, a, smem, grid, st);
-    case 5: return launch<2, true, MODE>(map, a, smem, grid, st);
-    case 6: return launch<3, false, MODE>(map, a, smem, grid, st);
-    case 7: return launch<3, true, MODE>(map, a, smem, grid, st);
+    case 2: return launch<1, false, 0, KIND>(map, a, smem, grid, st);
+    case 3: return launch<1, true, 0, KIND>(map, a, smem, grid, st);
+    case 4: return launch<2, false, 0, KIND>(map, a, smem, grid, st);
+    case 5: return launch<2, true, 0, KIND>(map, a, smem, grid, st);
+    case 6: return launch<3, false, 0, KIND>(map, a, smem, grid, st);
+    case 7: return launch<3, true, 0, KIND>(map, a, smem, grid, st);
   }
   return fail(CKINV_EINVAL, "sketch_tc: nsplit must be 1..3");
+}
+
+Error dispatch_dense(int nsplit, const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid, cudaStream_t st) {
+  switch (nsplit) {
+    case 1: return launch<1, false, 1, 0>(map, a, smem, grid, st);
+    case 2: return launch<2, false, 1, 0>(map, a, smem, grid, st);
+    case 3: return launch<3, false, 1, 0>(map, a, smem, grid, st);
+  }
+  return fail(CKINV_EINVAL, "dense_tc: nsplit must be 1..3");
 }
 
 // G[i * si + j * sj] = scale * sum_s part[s][i + j * ldp]   (FP64 sum over the splits)
@@ -507,6 +696,8 @@ __global__ void k_reduce_parts(int m, int d, int splits, const float *part, int6
 
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const KernelParams &kp, const float *points,
                 bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(points) & 15) != 0)
+    return fail(CKINV_EINVAL, "sketch: points must be 16-byte aligned for the tensor-core path");
   CK_TRY(omega_materialise_bf16(ctx, st));
   CUtensorMap map;
   TcArgs a;
@@ -519,7 +710,10 @@ Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const Ker
   a.pts = points;
   a.Y = Y;
   a.ldy = ldy;
-  return dispatch<0>(nsplit, deriv, map, a, smem, dim3((unsigned)ceil_div(n, BM), 1), st);
+  const dim3 grid((unsigned)ceil_div(n, BM), 1);
+  if (kp.kind == CKINV_SE) return dispatch_kernel<CKINV_SE>(nsplit, deriv, map, a, smem, grid, st);
+  if (kp.kind == CKINV_MATERN52) return dispatch_kernel<CKINV_MATERN52>(nsplit, deriv, map, a, smem, grid, st);
+  return fail(CKINV_EINVAL, "sketch_tc: covariance kind has no fused form");
 }
 
 Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const float *A, int64_t lda, double scale,
@@ -540,7 +734,7 @@ Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const fl
   if (Y) {
     a.Y = Y;
     a.ldy = ldy;
-    return dispatch<1>(nsplit, false, map, a, smem, dim3(mt, 1), st);
+    return dispatch_dense(nsplit, map, a, smem, dim3(mt, 1), st);
   }
   // split the contraction so that the grid covers every SM, then reduce in FP64
   int splits = std::max(1, std::min(a.num_kb, (ctx->sm_count + mt - 1) / mt));
@@ -551,7 +745,7 @@ Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const fl
   CK_CUDA(cudaMallocAsync((void **)&part, sizeof(float) * (size_t)splits * ldp * d, st));
   a.part = part;
   a.ldp = ldp;
-  Error e = dispatch<1>(nsplit, false, map, a, smem, dim3(mt, splits), st);
+  Error e = dispatch_dense(nsplit, map, a, smem, dim3(mt, splits), st);
   if (e.st == CKINV_OK) {
     note_launch();
     k_reduce_parts<<<(unsigned)std::min<int64_t>(ceil_div(m * d, 256), 2048), 256, 0, st>>>(
