@@ -80,11 +80,11 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: gives up after ~1 s or when another warp has flagged an abort.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                       bool cluster_scope = false) {
+// Bounded wait: gives up after ~1 s or when another warp has flagged an abort.  The first
+// poll is inline; the loop is not.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                            bool cluster_scope) {
   auto poll = [&]() { return cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); };
-  if (poll()) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (poll()) return true;
@@ -96,6 +96,11 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
       }
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          bool cluster_scope = false) {
+  if (cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, cluster_scope);
 }
 
 // Warp-wide bounded wait: every lane polls, so that each lane acquires the phase itself (no
@@ -253,13 +258,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b1_off = (uint32_t)(a.n0 / 2) * kRowBytes;
   const uint32_t rank = cluster_rank();       // 0: the CTA that issues the pair's MMAs
 
-  // fullA: this CTA's A tiles are written (one arrival per producer thread);
-  // fullB: this CTA's Omega half has landed;
+  // full: this CTA's A tiles are written (one arrival per producer thread) and its Omega
+  //   half has landed (the TMA thread's expect-tx arrival plus the bytes);
   // peerB (rank 0): the peer's A tiles and Omega half are ready (one cluster-scope arrival
   //   from the peer, made by a thread that does nothing else);
   // empty: the pair's MMAs are done with the stage (committed to both CTAs).
-  auto fullA = [&](int s) { return smem_u32(bars + s); };
-  auto fullB = [&](int s) { return smem_u32(bars + 8 + s); };
+  auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + 16 + s); };
   auto peerB = [&](int s) { return smem_u32(bars + 24 + s); };
   const uint32_t accum_bar = smem_u32(bars + 32);
@@ -281,8 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(fullA(s), 32 * kProducerWarps);
-      mbar_init(fullB(s), 1);
+      mbar_init(full(s), 32 * kProducerWarps + 1);
       mbar_init(empty(s), 1);
       mbar_init(peerB(s), 1);
     }
@@ -333,20 +336,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
         issue_points(kb + L);
         pts_issued = kb + L + 1;
-        mbar_arrive_expect_tx(fullB(s), b_bytes);
+        mbar_arrive_expect_tx(full(s), b_bytes);
         const int kx = (kb_begin + kb) * BK;
         const int h0 = a.n0 / 2, h1 = a.n1 / 2;
         for (int o = 0; o < h0; o += a.box_rows)
-          tma_load_2d(b_tile(s) + (uint32_t)o * kRowBytes, &tmapB, fullB(s), kx, (int)rank * h0 + o);
+          tma_load_2d(b_tile(s) + (uint32_t)o * kRowBytes, &tmapB, full(s), kx, (int)rank * h0 + o);
         for (int o = 0; o < h1; o += a.box_rows)
-          tma_load_2d(b_tile(s) + b1_off + (uint32_t)o * kRowBytes, &tmapB, fullB(s), kx, a.n0 + (int)rank * h1 + o);
+          tma_load_2d(b_tile(s) + b1_off + (uint32_t)o * kRowBytes, &tmapB, full(s), kx, a.n0 + (int)rank * h1 + o);
         ++issued;
       }
       // every copy this CTA issued must land before shared memory is released
       volatile int never = 0;
       int first = issued - S < 0 ? 0 : issued - S;
       for (int kb = first; kb < issued; ++kb)
-        mbar_wait(fullB(kb % S), (uint32_t)(kb / S) & 1u, &never);
+        mbar_wait(full(kb % S), (uint32_t)(kb / S) & 1u, &never);
       if (MODE == 0) {
         const int last = min(pts_issued, nkb);
         for (int kb = max(0, last - kPtSlots); kb < last; ++kb)
@@ -364,24 +367,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag) ||
-            !mbar_wait(peerB(s), ph, abort_flag, true)) {
+        if (!mbar_wait(full(s), ph, abort_flag) || !mbar_wait(peerB(s), ph, abort_flag, true)) {
           good = false;
           break;
         }
         tc_fence_after();
+        // a K step of 16 elements (32 bytes) adds 2 to the descriptor's start-address field
+        const uint64_t b0 = sw_desc(b_tile(s)), b1 = sw_desc(b_tile(s) + b1_off);
 #pragma unroll
         for (int t = 0; t < NSPLIT; ++t) {
+          const uint64_t a0 = sw_desc(a_tile(s, t));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            uint64_t ad = sw_desc(a_tile(s, t) + kk * 32);
-            uint64_t bd = sw_desc(b_tile(s) + kk * 32);
             uint32_t acc = (kb > 0 || t > 0 || kk > 0) ? 1u : 0u;
-            tc_mma_pair(tmem_base, ad, bd, id0, acc);
-            if (a.n1 > 0) {
-              uint64_t bd1 = sw_desc(b_tile(s) + b1_off + kk * 32);
-              tc_mma_pair(tmem_base + (uint32_t)a.n0, ad, bd1, id1, acc);
-            }
+            tc_mma_pair(tmem_base, a0 + 2 * kk, b0 + 2 * kk, id0, acc);
+            if (a.n1 > 0) tc_mma_pair(tmem_base + (uint32_t)a.n0, a0 + 2 * kk, b1 + 2 * kk, id1, acc);
           }
         }
         tc_commit_pair(empty(s), 0x3);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(fullA(s), ph, abort_flag) || !mbar_wait(fullB(s), ph, abort_flag)) break;
+        if (!mbar_wait(full(s), ph, abort_flag)) break;
         mbar_arrive_remote(peer_bar0 + 8u * (uint32_t)s);
       }
     }
@@ -450,88 +450,86 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag)) return false;
       if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag)) return false;
       const float *ps = pt_slots + (size_t)j * (kPtSlotBytes / 4) + (size_t)h * KH * a.dim;
+      // Phase 1: all CH * 8 entries of this lane's rows (no shared-memory store in between,
+      // so that the loads and the arithmetic of different entries overlap freely).
+      float kv[kRowsPerLane][CH * 8];
+      if (MODE == 0) {
+        // differences in scaled coordinates: x cs - p cs, with p raw and x pre-scaled
+        if (full_block && a.dim == 2) {
 #pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        float kv[kRowsPerLane][8];
-        if (MODE == 0) {
-          // differences in scaled coordinates: x cs - p cs, with p raw and x pre-scaled
-          if (full_block && a.dim == 2) {
+          for (int u = 0; u < CH * 8; u += 2) {
+            const float4 p2 = *reinterpret_cast<const float4 *>(ps + u * 2);   // points u, u + 1
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const float2 p = *reinterpret_cast<const float2 *>(ps + (c * 8 + u) * 2);
-#pragma unroll
-              for (int r = 0; r < kRowsPerLane; ++r) {
-                float dx = fmaf(-cs, p.x, xr[r][0]), dy = fmaf(-cs, p.y, xr[r][1]);
-                kv[r][u] = dev::kernel_value(KIND, fmaf(dy, dy, dx * dx), inv_l, DERIV);
-              }
-            }
-          } else if (full_block) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const float *q = ps + (c * 8 + u) * a.dim;
-              const float px = q[0], py = a.dim > 1 ? q[1] : 0.f, pz = a.dim > 2 ? q[2] : 0.f;
-#pragma unroll
-              for (int r = 0; r < kRowsPerLane; ++r) {
-                float dx = fmaf(-cs, px, xr[r][0]), dy = fmaf(-cs, py, xr[r][1]), dz = fmaf(-cs, pz, xr[r][2]);
-                kv[r][u] = dev::kernel_value(KIND, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), inv_l, DERIV);
-              }
-            }
-          } else {
-            // the last, partial block: points straight from global memory, zero past n
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int64_t k = kbase + c * 8 + u;
-              const bool valid = k < a.n;
-              const float *q = a.pts + (valid ? k : 0) * a.dim;
-              const float px = q[0], py = a.dim > 1 ? q[1] : 0.f, pz = a.dim > 2 ? q[2] : 0.f;
-#pragma unroll
-              for (int r = 0; r < kRowsPerLane; ++r) {
-                float dx = fmaf(-cs, px, xr[r][0]), dy = fmaf(-cs, py, xr[r][1]), dz = fmaf(-cs, pz, xr[r][2]);
-                float v = dev::kernel_value(KIND, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), inv_l, DERIV);
-                kv[r][u] = valid ? v : 0.0f;
-              }
+            for (int r = 0; r < kRowsPerLane; ++r) {
+              float dx = fmaf(-cs, p2.x, xr[r][0]), dy = fmaf(-cs, p2.y, xr[r][1]);
+              kv[r][u] = dev::kernel_value(KIND, fmaf(dy, dy, dx * dx), inv_l, DERIV);
+              dx = fmaf(-cs, p2.z, xr[r][0]);
+              dy = fmaf(-cs, p2.w, xr[r][1]);
+              kv[r][u + 1] = dev::kernel_value(KIND, fmaf(dy, dy, dx * dx), inv_l, DERIV);
             }
           }
         } else {
-          const int64_t k0 = kbase + c * 8;
+          // other dimensions, or the last, partial block (points from global memory, zero
+          // past n)
 #pragma unroll
-          for (int j = 0; j < kRowsPerLane; ++j) {
-            if (rok[j] && k0 + 8 <= a.n) {
-              float4 lo = *reinterpret_cast<const float4 *>(arow[j] + k0);
-              float4 hi = *reinterpret_cast<const float4 *>(arow[j] + k0 + 4);
-              kv[j][0] = lo.x; kv[j][1] = lo.y; kv[j][2] = lo.z; kv[j][3] = lo.w;
-              kv[j][4] = hi.x; kv[j][5] = hi.y; kv[j][6] = hi.z; kv[j][7] = hi.w;
-            } else {
+          for (int u = 0; u < CH * 8; ++u) {
+            const int64_t k = kbase + u;
+            const bool valid = full_block || k < a.n;
+            const float *q = full_block ? ps + u * a.dim : a.pts + (valid ? k : 0) * a.dim;
+            const float px = q[0], py = a.dim > 1 ? q[1] : 0.f, pz = a.dim > 2 ? q[2] : 0.f;
 #pragma unroll
-              for (int u = 0; u < 8; ++u) kv[j][u] = (rok[j] && k0 + u < a.n) ? arow[j][k0 + u] : 0.0f;
+            for (int r = 0; r < kRowsPerLane; ++r) {
+              float dx = fmaf(-cs, px, xr[r][0]), dy = fmaf(-cs, py, xr[r][1]), dz = fmaf(-cs, pz, xr[r][2]);
+              float v = dev::kernel_value(KIND, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), inv_l, DERIV);
+              kv[r][u] = valid ? v : 0.0f;
             }
           }
         }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kRowsPerLane; ++r) {
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int64_t k0 = kbase + c * 8;
+            if (rok[r] && k0 + 8 <= a.n) {
+              float4 lo = *reinterpret_cast<const float4 *>(arow[r] + k0);
+              float4 hi = *reinterpret_cast<const float4 *>(arow[r] + k0 + 4);
+              kv[r][c * 8 + 0] = lo.x; kv[r][c * 8 + 1] = lo.y; kv[r][c * 8 + 2] = lo.z; kv[r][c * 8 + 3] = lo.w;
+              kv[r][c * 8 + 4] = hi.x; kv[r][c * 8 + 5] = hi.y; kv[r][c * 8 + 6] = hi.z; kv[r][c * 8 + 7] = hi.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) kv[r][c * 8 + u] = (rok[r] && k0 + u < a.n) ? arow[r][k0 + u] : 0.0f;
+            }
+          }
+        }
+      }
+      // Phase 2: split into BF16 terms and store each 16-byte chunk at its swizzled place.
+      uint8_t *stage_base = tiles + (size_t)s * stage_bytes;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
         const uint32_t off = lane_base + (swz_chunk((uint32_t)(h * CH + c), (uint32_t)lane) << 4);
 #pragma unroll
-        for (int j = 0; j < kRowsPerLane; ++j) {
+        for (int r = 0; r < kRowsPerLane; ++r) {
 #pragma unroll
           for (int t = 0; t < NSPLIT; ++t) {
             uint32_t w[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              __nv_bfloat162 b2 = __floats2bfloat162_rn(kv[j][2 * u], kv[j][2 * u + 1]);
+              __nv_bfloat162 b2 = __floats2bfloat162_rn(kv[r][c * 8 + 2 * u], kv[r][c * 8 + 2 * u + 1]);
               w[u] = *reinterpret_cast<uint32_t *>(&b2);
               if (t + 1 < NSPLIT) {
                 float2 back = __bfloat1622float2(b2);
-                kv[j][2 * u] -= back.x;
-                kv[j][2 * u + 1] -= back.y;
+                kv[r][c * 8 + 2 * u] -= back.x;
+                kv[r][c * 8 + 2 * u + 1] -= back.y;
               }
             }
-            const uint32_t dst = a_tile(s, t) + off + (uint32_t)(j * 32) * kRowBytes;
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]),
-                         "r"(w[2]), "r"(w[3])
-                         : "memory");
+            *reinterpret_cast<uint4 *>(stage_base + (size_t)t * kATileBytes + off + (uint32_t)(r * 32) * kRowBytes) =
+                make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
       }
       fence_async_smem();                  // this thread's tile writes -> visible to the tensor core
-      mbar_arrive(fullA(s));
+      mbar_arrive(full(s));
       return true;
     };
     for (int kb = 0; kb < nkb; ++kb) {
