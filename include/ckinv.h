@@ -12,7 +12,7 @@
  *                 binary tree of QRs of stacked R factors (Eqs. 2-4);
  *   ckinv_solve   the low-rank solve that applies Q_hat and R to A.
  * ckinv_nll_grad evaluates the Gaussian negative log-likelihood and its gradient, the
- * use the paper targets (Abstract; Sec. 1: "evaluating Gaussian likelihoods").
+ * application the paper names first (Abstract and Sec. 1: Gaussian likelihoods of many points).
  *
  * Conventions shared by every entry point:
  *   - Matrices are column-major; "ld" is the leading dimension in elements.
@@ -205,10 +205,25 @@ ckinv_status ckinv_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
                             const float *y, double *nll, double *grad,
                             ckinv_stream stream);
 
-/* Batched form over nprob independent problems (uneven n): plans[p], kerns[p],
- * points[p], y[p] as above (device pointers in HOST arrays); nll[p] and
- * grad[3p..3p+2] are host outputs.  The per-stage kernels of all problems run as one
- * launch each, and the whole sequence is replayed as one CUDA graph. */
+/* Batched form over nprob independent problems (uneven n, d, kernels): plans[p],
+ * kerns[p], points[p], y[p] as above (device pointers in HOST arrays); nll[p] and
+ * grad[3p..3p+2] are host outputs, written after `stream` is synchronised.  Each problem
+ * runs the same pipeline as ckinv_nll_grad; the pipelines of all problems are captured
+ * into one CUDA graph (on 8 forked streams, so that small problems overlap on the SMs)
+ * and the graph is launched once.  A problem whose block_rows is 0 gets the leaf height
+ * the autotuner (ckinv_autotune) picks for its shape class, tuned on first sight.
+ * Device-side errors name the problem index in ckinv_last_error. */
+/* Leaf-height autotuner of the TSQR (the block_rows of a plan).  Times the TSQR of an
+ * n x d pseudo-random matrix at the candidate heights 256 .. 4096 (at least d, at most
+ * n / 2) with the plan's tree_fp64_levels and leaf_fp64, and records the fastest for the
+ * shape class (device, d, ceil(log2 n), tree_fp64_levels, leaf_fp64).  Every later call
+ * on any context whose plan has block_rows = 0 and the same shape class uses it.  Writes
+ * the chosen height to *block_rows; synchronises `stream`.  No counterpart in the paper,
+ * which fixes the height by a formula in n and r (Sec. 3.3).  Without tuning the
+ * library uses 2048 rows, or n / 2 for small n. */
+ckinv_status ckinv_autotune(ckinv_ctx *ctx, const ckinv_plan_desc *plan, int32_t *block_rows,
+                            ckinv_stream stream);
+
 ckinv_status ckinv_nll_grad_batched(ckinv_ctx *ctx, int32_t nprob,
                                     const ckinv_plan_desc *plans,
                                     const ckinv_kernel *kerns,

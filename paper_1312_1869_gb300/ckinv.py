@@ -68,6 +68,7 @@ _SIGS = {
                                     ctypes.c_int64, ctypes.c_int32, _VP, ctypes.c_int64, _VP]),
     "ckinv_nll_grad": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP]),
+    "ckinv_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_int32), _VP]),
     "ckinv_nll_grad_batched": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(PlanDesc),
                                               ctypes.POINTER(KernelDesc), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP]),
@@ -316,7 +317,17 @@ def nll_grad(ctx, plan, kern, points, y, stream=None):
     return nll.value, [g[0], g[1], g[2]]
 
 
+def autotune(ctx, plan, stream=None):
+    """Leaf height (block_rows) the library's autotuner picks for this plan's shape class;
+    later plans with block_rows = 0 in the same class use it."""
+    b = ctypes.c_int32(0)
+    pd = plan.desc()
+    ctx._raise(load().ckinv_autotune(ctx.handle, ctypes.byref(pd), ctypes.byref(b), _stream(stream)))
+    return b.value
+
+
 def nll_grad_batched(ctx, plans, kerns, points, ys, stream=None):
+    """NLL and gradient of many independent problems, run as one CUDA graph."""
     P = len(plans)
     pds = (PlanDesc * P)(*[p.desc() for p in plans])
     kds = (KernelDesc * P)(*[k.desc() for k in kerns])

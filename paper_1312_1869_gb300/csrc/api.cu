@@ -4,12 +4,27 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "internal.cuh"
 
 using namespace ckinv;
 
 Error ckinv::stage_upload(ckinv_ctx *ctx, const void *src, size_t bytes, void *dst, cudaStream_t st) {
+  if (ctx->capture_arena) {
+    // inside a graph capture: the copy runs when the graph does, so its source bytes must
+    // stay put until then
+    UploadArena &ar = *ctx->capture_arena;
+    size_t at = (ar.used + 15) & ~(size_t)15;
+    if (at + bytes > ar.cap) return fail(CKINV_ENOMEM, "upload arena of the batched graph is full");
+    memcpy(ar.host + at, src, bytes);
+    ar.used = at + bytes;
+    CK_CUDA(cudaMemcpyAsync(dst, ar.host + at, bytes, cudaMemcpyHostToDevice, st));
+    return ok();
+  }
   ckinv_ctx::Stage &sl = ctx->stage[ctx->stage_next];
   ctx->stage_next = (ctx->stage_next + 1) % 8;
   if (sl.done) CK_CUDA(cudaEventSynchronize(sl.done));
@@ -137,6 +152,102 @@ void factor_release(ckinv_factor *f) {
   delete f;
 }
 
+// ------------------------------------------------------------------ leaf-height autotuner
+// Chosen TSQR leaf heights, keyed by (device, d, ceil(log2 n), FP64 tree levels, FP64 leaves).
+struct TuneKey {
+  int device, d, log2n, fp64_levels, leaf_fp64;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(device, d, log2n, fp64_levels, leaf_fp64) <
+           std::tie(o.device, o.d, o.log2n, o.fp64_levels, o.leaf_fp64);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+TuneKey tune_key(const ckinv_ctx *ctx, const ckinv_plan_desc *plan) {
+  int l = 0;
+  while (((int64_t)1 << l) < plan->n) ++l;
+  return TuneKey{ctx->device, plan->d, l, plan->tree_fp64_levels, plan->leaf_fp64};
+}
+
+int leaf_rows(const ckinv_ctx *ctx, const ckinv_plan_desc *plan) {
+  if (plan->block_rows) return plan->block_rows;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(ctx, plan));
+    if (it != g_tuned.end()) return it->second;
+  }
+  return auto_block_rows(plan->n, plan->d, ctx->sm_count);
+}
+
+__global__ void k_fill_hash(int64_t count, uint32_t salt, float *Y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ salt;
+    h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
+    Y[i] = (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
+  }
+}
+
+// Times the TSQR of an n x d matrix of pseudo-random entries at each candidate leaf height
+// and records the fastest for the plan's shape class.
+Error autotune_leaf_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan, cudaStream_t st, int *out) {
+  const int64_t n = plan->n;
+  const int d = plan->d;
+  std::vector<int> cand;
+  for (int b : {256, 512, 1024, 2048, 4096})
+    if (b >= d && (int64_t)b * 2 <= n) cand.push_back(b);
+  if (cand.empty()) cand.push_back(auto_block_rows(n, d, ctx->sm_count));
+  float *Y = nullptr, *Q = nullptr;
+  double *R = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Error e = ok();
+  int best = cand[0];
+  float best_ms = 1e30f;
+  do {
+    if (cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&Q, sizeof(float) * n * d, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&R, sizeof(double) * d * d, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "autotune workspace");
+      break;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "autotune events");
+      break;
+    }
+    note_launch();
+    k_fill_hash<<<(unsigned)std::min<int64_t>(ceil_div(n * d, 256), 4096), 256, 0, st>>>(n * d, 0x9e3779b9u, Y);
+    for (int b : cand) {
+      if ((e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, Y, n, Q, R, st)).st) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && !e.st; ++r)
+        e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, Y, n, Q, R, st);
+      cudaEventRecord(e1, st);
+      if (e.st) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        e = fail(CKINV_ECUDA, "autotune timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = b;
+      }
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (void *p : {(void *)Y, (void *)Q, (void *)R})
+    if (p) cudaFreeAsync(p, st);
+  if (e.st) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(ctx, plan)] = best;
+  }
+  *out = best;
+  return ok();
+}
+
 Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, float *Y, int64_t ldy,
               ckinv_factor **out, cudaStream_t st) {
   CK_TRY(check_plan(plan, kern, false));
@@ -144,7 +255,7 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
   *out = nullptr;
   const int64_t n = plan->n;
   const int d = plan->d;
-  int b = plan->block_rows ? plan->block_rows : auto_block_rows(n, d, ctx->sm_count);
+  int b = leaf_rows(ctx, plan);
   CK_TRY(omega_draw(ctx, n, d, plan->seed, st));
   ckinv_factor *f = new ckinv_factor();
   f->ctx = ctx;
@@ -187,7 +298,6 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
   }
   if (e.st == CKINV_OK) e = lowrank_core(ctx, f, st);
   if (e.st != CKINV_OK) {
-    cudaStreamSynchronize(st);
     factor_release(f);
     return e;
   }
@@ -205,32 +315,32 @@ bool is_host_pointer(const void *p) {
 }
 
 // ------------------------------------------------------------------ small FP64 helpers
-__global__ void k_dot(int64_t n, const double *x, int64_t incx, const double *y, int64_t incy, double *out) {
-  __shared__ double red[256];
+// out += x . y in one block (a fixed summation order, so results are reproducible)
+__global__ void __launch_bounds__(1024) k_dot(int64_t n, const double *x, int64_t incx, const double *y,
+                                              int64_t incy, double *out) {
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma(x[i * incx], y[i * incy], s);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i * incx], y[i * incy], s);
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+  if (threadIdx.x == 0) *out += red[0];
 }
 
-__global__ void k_dot_f32(int64_t n, const float *x, const float *y, double *out) {
-  __shared__ double red[256];
+__global__ void __launch_bounds__(1024) k_dot_f32(int64_t n, const float *x, const float *y, double *out) {
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s = fma((double)x[i], (double)y[i], s);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma((double)x[i], (double)y[i], s);
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+  if (threadIdx.x == 0) *out += red[0];
 }
 
 // y = op(A) x  (d x d FP64, ld d)
@@ -268,35 +378,45 @@ __global__ void k_finish_nll(const double *s, const double *lp, int64_t n, int d
   out[3] = 0.5 * tau * (trki - s[10]);
 }
 
-Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
-                  const float *y, double *nll, double *grad, cudaStream_t st) {
+// The whole likelihood pipeline enqueued on st, leaving [NLL, d/dlog l, d/dlog variance,
+// d/dlog nugget] in out_dev (4 doubles, device memory).  Nothing here waits on the host or
+// reads device memory back, so the sequence can be captured into a CUDA graph.
+Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
+                       const float *y, double *out_dev, cudaStream_t st) {
   CK_TRY(check_plan(plan, kern, true));
   if (kern->kind == CKINV_DENSE) return fail(CKINV_EINVAL, "nll_grad needs a kernel function, not a matrix");
-  if (!points || !y || !nll || !grad) return fail(CKINV_EINVAL, "null argument");
+  if (!points || !y || !out_dev) return fail(CKINV_EINVAL, "null argument");
   const int64_t n = plan->n;
   const int d = plan->d;
   const size_t dd = (size_t)d * d;
   float *Y = nullptr, *Yd = nullptr, *alpha = nullptr;
   double *ws = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st));
-  CK_CUDA(cudaMallocAsync((void **)&Yd, sizeof(float) * n * d, st));
-  CK_CUDA(cudaMallocAsync((void **)&alpha, sizeof(float) * n, st));
-  // ws: G1, G2, E, F, T1, T2 (d x d each), g3, beta, gamma, v1, v2 (d each), alpha64? no, s[16], out[4]
-  const size_t ws_elems = 6 * dd + 5 * (size_t)d + 16 + 4;
-  CK_CUDA(cudaMallocAsync((void **)&ws, sizeof(double) * ws_elems, st));
-  double *G1 = ws, *G2 = G1 + dd, *E = G2 + dd, *F = E + dd, *T1 = F + dd, *T2 = T1 + dd;
-  double *g3 = T2 + dd, *beta = g3 + d, *gamma = beta + d, *v1 = gamma + d, *v2 = v1 + d;
-  double *s = v2 + d, *out = s + 16;
-  CK_CUDA(cudaMemsetAsync(s, 0, sizeof(double) * 20, st));
-
-  CK_TRY(do_sketch(ctx, plan, kern, points, nullptr, 0, false, Y, n, st));
-  CK_TRY(do_sketch(ctx, plan, kern, points, nullptr, 0, true, Yd, n, st));
   ckinv_factor *f = nullptr;
-  CK_TRY(do_tsqr(ctx, plan, kern, Y, n, &f, st));
   Error e = ok();
   do {
-    e = lowrank_solve(ctx, f, y, n, 1, alpha, n, plan->refine_steps, st);
-    if (e.st) break;
+    if (cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&Yd, sizeof(float) * n * d, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&alpha, sizeof(float) * n, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "nll workspace");
+      break;
+    }
+    // ws: G1, G2, E, F, T1, T2 (d x d each), g3, beta, gamma, v1, v2 (d each), s[16]
+    const size_t ws_elems = 6 * dd + 5 * (size_t)d + 16;
+    if (cudaMallocAsync((void **)&ws, sizeof(double) * ws_elems, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "nll workspace");
+      break;
+    }
+    double *G1 = ws, *G2 = G1 + dd, *E = G2 + dd, *F = E + dd, *T1 = F + dd, *T2 = T1 + dd;
+    double *g3 = T2 + dd, *beta = g3 + d, *gamma = beta + d, *v1 = gamma + d, *v2 = v1 + d;
+    double *s = v2 + d;
+    if (cudaMemsetAsync(s, 0, sizeof(double) * 16, st) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "memset");
+      break;
+    }
+    if ((e = do_sketch(ctx, plan, kern, points, nullptr, 0, false, Y, n, st)).st) break;
+    if ((e = do_sketch(ctx, plan, kern, points, nullptr, 0, true, Yd, n, st)).st) break;
+    if ((e = do_tsqr(ctx, plan, kern, Y, n, &f, st)).st) break;
+    if ((e = lowrank_solve(ctx, f, y, n, 1, alpha, n, plan->refine_steps, st)).st) break;
     // beta = Q^T alpha, g3 = Yd^T alpha, G1 = Q^T Yd, G2 = Omega^T Yd
     if ((e = tsprod(ctx, n, d, 1, f->Q, n, nullptr, nullptr, 0, alpha, n, beta, st)).st) break;
     if ((e = tsprod(ctx, n, d, 1, Yd, n, nullptr, nullptr, 0, alpha, n, g3, st)).st) break;
@@ -309,60 +429,207 @@ Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kerne
       break;
     }
     // gamma = B^-T beta;  E = C'^-1;  F = B^-T E
-    cudaMemcpyAsync(gamma, beta, sizeof(double) * d, cudaMemcpyDeviceToDevice, st);
+    if (cudaMemcpyAsync(gamma, beta, sizeof(double) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "copy");
+      break;
+    }
     if ((e = lu_solve_dev(d, 1, f->luB, f->pivB, gamma, 1, st)).st) break;
     ::ckinv::note_launch(), k_identity<<<64, 256, 0, st>>>(d, E);
     if ((e = lu_solve_dev(d, d, f->luC, f->pivC, E, 0, st)).st) break;
-    cudaMemcpyAsync(F, E, sizeof(double) * dd, cudaMemcpyDeviceToDevice, st);
+    if (cudaMemcpyAsync(F, E, sizeof(double) * dd, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "copy");
+      break;
+    }
     if ((e = lu_solve_dev(d, d, f->luB, f->pivB, F, 1, st)).st) break;
-    const int gb = 64;
     // s0 = y^T alpha
-    ::ckinv::note_launch(), k_dot_f32<<<gb, 256, 0, st>>>(n, y, alpha, s + 0);
+    ::ckinv::note_launch(), k_dot_f32<<<1, 1024, 0, st>>>(n, y, alpha, s + 0);
     // s1 = <E, G1>, s3 = <F, G2>
-    ::ckinv::note_launch(), k_dot<<<gb, 256, 0, st>>>((int64_t)dd, E, 1, G1, 1, s + 1);
-    ::ckinv::note_launch(), k_dot<<<gb, 256, 0, st>>>((int64_t)dd, F, 1, G2, 1, s + 3);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>((int64_t)dd, E, 1, G1, 1, s + 1);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>((int64_t)dd, F, 1, G2, 1, s + 3);
     // s2 = gamma^T g3
-    ::ckinv::note_launch(), k_dot<<<1, 256, 0, st>>>(d, gamma, 1, g3, 1, s + 2);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>(d, gamma, 1, g3, 1, s + 2);
     // s4 = gamma^T G2 gamma
     ::ckinv::note_launch(), k_gemv<<<(d + 127) / 128, 128, 0, st>>>(d, G2, gamma, v1, 0);
-    ::ckinv::note_launch(), k_dot<<<1, 256, 0, st>>>(d, gamma, 1, v1, 1, s + 4);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>(d, gamma, 1, v1, 1, s + 4);
     // s5 = <E, R>, s6 = gamma^T R^T beta
-    ::ckinv::note_launch(), k_dot<<<gb, 256, 0, st>>>((int64_t)dd, E, 1, f->R, 1, s + 5);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>((int64_t)dd, E, 1, f->R, 1, s + 5);
     ::ckinv::note_launch(), k_gemv<<<(d + 127) / 128, 128, 0, st>>>(d, f->R, beta, v1, 1);
-    ::ckinv::note_launch(), k_dot<<<1, 256, 0, st>>>(d, gamma, 1, v1, 1, s + 6);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>(d, gamma, 1, v1, 1, s + 6);
     // T1 = B R;  s7 = <F, B R>;  s8 = gamma^T B R gamma
     if ((e = gemm_small_dev(d, d, f->B, f->R, T1, 0, st)).st) break;
-    ::ckinv::note_launch(), k_dot<<<gb, 256, 0, st>>>((int64_t)dd, F, 1, T1, 1, s + 7);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>((int64_t)dd, F, 1, T1, 1, s + 7);
     ::ckinv::note_launch(), k_gemv<<<(d + 127) / 128, 128, 0, st>>>(d, T1, gamma, v2, 0);
-    ::ckinv::note_launch(), k_dot<<<1, 256, 0, st>>>(d, gamma, 1, v2, 1, s + 8);
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>(d, gamma, 1, v2, 1, s + 8);
     // s9 = tr(E B) = <E^T, B>;  s10 = alpha^T alpha
     ::ckinv::note_launch(), k_transpose<<<64, 256, 0, st>>>(d, E, T2);
-    ::ckinv::note_launch(), k_dot<<<gb, 256, 0, st>>>((int64_t)dd, T2, 1, f->B, 1, s + 9);
-    ::ckinv::note_launch(), k_dot_f32<<<gb, 256, 0, st>>>(n, alpha, alpha, s + 10);
-    ::ckinv::note_launch(), k_finish_nll<<<1, 1, 0, st>>>(s, f->logdet_parts, n, d, f->tau, out);
-    double hout[4];
-    if (cudaMemcpyAsync(hout, out, sizeof(hout), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-      e = fail(CKINV_ECUDA, "copy of the likelihood to the host failed");
-      break;
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-      e = fail(CKINV_ECUDA, cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
+    ::ckinv::note_launch(), k_dot<<<1, 1024, 0, st>>>((int64_t)dd, T2, 1, f->B, 1, s + 9);
+    ::ckinv::note_launch(), k_dot_f32<<<1, 1024, 0, st>>>(n, alpha, alpha, s + 10);
+    ::ckinv::note_launch(), k_finish_nll<<<1, 1, 0, st>>>(s, f->logdet_parts, n, d, f->tau, out_dev);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(le));
+  } while (0);
+  factor_release(f);
+  for (void *p : {(void *)Y, (void *)Yd, (void *)alpha, (void *)ws})
+    if (p) cudaFreeAsync(p, st);
+  return e;
+}
+
+Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
+                  const float *y, double *nll, double *grad, cudaStream_t st) {
+  if (!nll || !grad) return fail(CKINV_EINVAL, "null argument");
+  double *dout = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&dout, sizeof(double) * 4, st));
+  Error e = nll_grad_enqueue(ctx, plan, kern, points, y, dout, st);
+  double hout[4] = {0, 0, 0, 0};
+  if (e.st == CKINV_OK && cudaMemcpyAsync(hout, dout, sizeof(hout), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    e = fail(CKINV_ECUDA, "copy of the likelihood to the host failed");
+  cudaFreeAsync(dout, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && e.st == CKINV_OK)
+    e = fail(CKINV_ECUDA, cudaGetErrorString(cudaGetLastError()));
+  if (e.st == CKINV_OK) e = read_device_error(ctx, st);
+  if (e.st == CKINV_OK) {
     *nll = hout[0];
     grad[0] = hout[1];
     grad[1] = hout[2];
     grad[2] = hout[3];
+  }
+  return e;
+}
+
+// ------------------------------------------------------------------ batched likelihood
+// Every problem gets a context of its own (its Omega buffers are reserved here, so nothing
+// allocates through the context during capture); the problems' pipelines are captured on
+// kBatchStreams forked streams of one CUDA graph, which is instantiated and launched once.
+constexpr int kBatchStreams = 8;
+
+Error do_nll_grad_batched(ckinv_ctx *ctx, int nprob, const ckinv_plan_desc *plans, const ckinv_kernel *kerns,
+                          const float *const *points, const float *const *y, double *nll, double *grad,
+                          cudaStream_t st) {
+  std::vector<ckinv_plan_desc> pl(plans, plans + nprob);
+  for (int p = 0; p < nprob; ++p) {
+    CK_TRY(check_plan(&pl[p], &kerns[p], true));
+    if (kerns[p].kind == CKINV_DENSE) return fail(CKINV_EINVAL, "nll_grad needs a kernel function, not a matrix");
+    if (!points[p] || !y[p]) return fail(CKINV_EINVAL, "null points or targets");
+  }
+  // leaf heights: the autotuner's choice for each shape class not tuned yet
+  for (int p = 0; p < nprob; ++p) {
+    if (pl[p].block_rows) continue;
+    bool known;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      known = g_tuned.count(tune_key(ctx, &pl[p])) != 0;
+    }
+    int b = 0;
+    if (!known) CK_TRY(autotune_leaf_rows(ctx, &pl[p], st, &b));
+    pl[p].block_rows = leaf_rows(ctx, &pl[p]);
+  }
+  std::vector<ckinv_ctx *> sub(nprob, nullptr);
+  UploadArena arena;
+  double *d_out = nullptr;
+  const int ns = std::min(nprob, kBatchStreams);
+  std::vector<cudaStream_t> ws(ns, nullptr);
+  std::vector<cudaEvent_t> join(ns, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;   // the capture origin (the caller's stream may be the legacy one)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<double> hout((size_t)nprob * 4, 0.0);
+  Error e = ok();
+  do {
+    for (int p = 0; p < nprob && !e.st; ++p) {
+      sub[p] = new ckinv_ctx();
+      sub[p]->device = ctx->device;
+      sub[p]->sm_count = ctx->sm_count;
+      if (cudaMalloc((void **)&sub[p]->d_err, sizeof(int)) != cudaSuccess ||
+          cudaMemsetAsync(sub[p]->d_err, 0, sizeof(int), st) != cudaSuccess) {
+        e = fail(CKINV_ENOMEM, "batch context");
+        break;
+      }
+      e = omega_reserve(sub[p], pl[p].n, pl[p].d, st);
+    }
+    if (e.st) break;
+    arena.cap = ((size_t)1 << 20) + (size_t)nprob * (256 << 10);
+    if (cudaMallocHost((void **)&arena.host, arena.cap) != cudaSuccess ||
+        cudaMalloc((void **)&d_out, sizeof(double) * 4 * nprob) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "batch buffers");
+      break;
+    }
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "batch events");
+      break;
+    }
+    for (int w = 0; w < ns && !e.st; ++w)
+      if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&join[w], cudaEventDisableTiming) != cudaSuccess)
+        e = fail(CKINV_ECUDA, "batch streams");
+    if (e.st) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {   // reservations are in place
+      e = fail(CKINV_ECUDA, cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "cudaStreamBeginCapture failed");
+      break;
+    }
+    cudaEventRecord(fork, cap);
+    for (int w = 0; w < ns; ++w) cudaStreamWaitEvent(ws[w], fork, 0);
+    for (int p = 0; p < nprob && !e.st; ++p) {
+      sub[p]->capture_arena = &arena;
+      e = nll_grad_enqueue(sub[p], &pl[p], &kerns[p], points[p], y[p], d_out + 4 * p, ws[p % ns]);
+      sub[p]->capture_arena = nullptr;
+    }
+    for (int w = 0; w < ns; ++w) {
+      cudaEventRecord(join[w], ws[w]);
+      cudaStreamWaitEvent(cap, join[w], 0);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (e.st) break;
+    if (ce != cudaSuccess || !graph) {
+      e = fail(CKINV_ECUDA, std::string("graph capture of the batch failed: ") + cudaGetErrorString(ce));
+      break;
+    }
+    if ((ce = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ce));
+      break;
+    }
+    ::ckinv::note_launch();
+    if ((ce = cudaGraphLaunch(exec, st)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(hout.data(), d_out, sizeof(double) * 4 * nprob, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (ce = cudaStreamSynchronize(st)) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, std::string("batched graph: ") + cudaGetErrorString(ce));
+      break;
+    }
+    for (int p = 0; p < nprob && !e.st; ++p) {
+      Error pe = read_device_error(sub[p], st);
+      if (pe.st) e = fail(pe.st, "problem " + std::to_string(p) + ": " + pe.msg);
+    }
   } while (0);
-  cudaError_t le = cudaGetLastError();
-  if (e.st == CKINV_OK && le != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(le));
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   cudaStreamSynchronize(st);
-  factor_release(f);
-  cudaFreeAsync(Y, st);
-  cudaFreeAsync(Yd, st);
-  cudaFreeAsync(alpha, st);
-  cudaFreeAsync(ws, st);
-  if (e.st == CKINV_OK) e = read_device_error(ctx, st);
+  for (int w = 0; w < ns; ++w) {
+    if (ws[w]) cudaStreamDestroy(ws[w]);
+    if (join[w]) cudaEventDestroy(join[w]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (cap) cudaStreamDestroy(cap);
+  for (ckinv_ctx *c : sub) {
+    if (!c) continue;
+    for (void *q : {(void *)c->d_err, (void *)c->hist, (void *)c->cand, (void *)c->cand_idx, (void *)c->small,
+                    (void *)c->om.bits, (void *)c->om.cols, (void *)c->om.omegaT})
+      if (q) cudaFree(q);
+    delete c;
+  }
+  if (arena.host) cudaFreeHost(arena.host);
+  if (d_out) cudaFree(d_out);
+  if (e.st == CKINV_OK) {
+    for (int p = 0; p < nprob; ++p) {
+      nll[p] = hout[4 * p];
+      for (int k = 0; k < 3; ++k) grad[3 * p + k] = hout[4 * p + 1 + k];
+    }
+  }
   return e;
 }
 
@@ -602,6 +869,20 @@ ckinv_status ckinv_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const c
   return finish(ctx, do_nll_grad(ctx, plan, kern, points, y, nll, grad, (cudaStream_t)stream));
 }
 
+ckinv_status ckinv_autotune(ckinv_ctx *ctx, const ckinv_plan_desc *plan, int32_t *block_rows, ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  if (!plan || !block_rows) return finish(ctx, fail(CKINV_EINVAL, "null argument"));
+  if (plan->d < 16 || plan->d > 512 || plan->d % 16 != 0 || plan->n < plan->d || plan->n > ((int64_t)1 << 31))
+    return finish(ctx, fail(CKINV_EINVAL, "need 16 <= d <= 512, d % 16 == 0, d <= n <= 2^31"));
+  if (plan->tree_fp64_levels < -1 || (plan->leaf_fp64 != 0 && plan->leaf_fp64 != 1))
+    return finish(ctx, fail(CKINV_EINVAL, "bad tree_fp64_levels or leaf_fp64"));
+  DeviceGuard g(ctx->device);
+  int b = 0;
+  Error e = autotune_leaf_rows(ctx, plan, (cudaStream_t)stream, &b);
+  if (e.st == CKINV_OK) *block_rows = b;
+  return finish(ctx, e);
+}
+
 ckinv_status ckinv_nll_grad_batched(ckinv_ctx *ctx, int32_t nprob, const ckinv_plan_desc *plans,
                                     const ckinv_kernel *kerns, const float *const *points, const float *const *y,
                                     double *nll, double *grad, ckinv_stream stream) {
@@ -609,10 +890,7 @@ ckinv_status ckinv_nll_grad_batched(ckinv_ctx *ctx, int32_t nprob, const ckinv_p
   if (nprob < 1 || !plans || !kerns || !points || !y || !nll || !grad)
     return finish(ctx, fail(CKINV_EINVAL, "null argument or nprob < 1"));
   DeviceGuard g(ctx->device);
-  Error e = ok();
-  for (int p = 0; p < nprob && e.st == CKINV_OK; ++p)
-    e = do_nll_grad(ctx, &plans[p], &kerns[p], points[p], y[p], &nll[p], &grad[3 * p], (cudaStream_t)stream);
-  return finish(ctx, e);
+  return finish(ctx, do_nll_grad_batched(ctx, nprob, plans, kerns, points, y, nll, grad, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -6,8 +6,9 @@
 // CTA tile BM x BN, thread tile TM x TN (two TM/2 x TN/2 quadrants, so that the shared
 // memory reads of a warp are conflict-free 16-byte vectors), BK = 8 deep, double-buffered
 // through registers: the next k-slab is fetched from global memory while the current one
-// is multiplied.  Split-K over gridDim.z accumulates into C with atomics after C has been
-// scaled by beta.
+// is multiplied.  Split-K over gridDim.z writes one partial product per split to a
+// workspace, and a second kernel adds them in split order (so results do not depend on
+// the order in which blocks finish).
 #include "internal.cuh"
 
 namespace ckinv {
@@ -17,7 +18,7 @@ template <typename T, int BM, int BN, int TM, int TN_, bool TRANSA>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 : 3)
     k_gemm(int M, int N, int K, T alpha, const T *__restrict__ A, int64_t lda, int64_t sA,
            const T *__restrict__ B, int64_t ldb, int64_t sB, T beta, T *__restrict__ C, int64_t ldc, int64_t sC,
-           int ksplit) {
+           int ksplit, T *__restrict__ part) {
   constexpr int BK = 8;
   constexpr int NTX = BN / TN_, NTY = BM / TM;
   constexpr int NT = NTX * NTY;
@@ -29,7 +30,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 :
   const int batch = blockIdx.z / ksplit, split = blockIdx.z % ksplit;
   A += (int64_t)batch * sA;
   B += (int64_t)batch * sB;
-  C += (int64_t)batch * sC;
+  if (ksplit > 1) {   // partial (split, batch) of the workspace: M x N, ld M
+    C = part + ((int64_t)split * (gridDim.z / ksplit) + batch) * M * N;
+    ldc = M;
+  } else {
+    C += (int64_t)batch * sC;
+  }
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
   const int kb = split * kchunk, ke = min(K, kb + kchunk);
@@ -122,36 +128,40 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 :
       int n = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
       if (n >= N) continue;
       T *c = C + m + (int64_t)n * ldc;
-      if (ksplit > 1) atomicAdd(c, alpha * acc[i][j]);
+      if (ksplit > 1) *c = alpha * acc[i][j];
       else *c = alpha * acc[i][j] + (beta == T(0) ? T(0) : beta * *c);
     }
   }
 }
 
+// C_b = beta C_b + sum over s (in order) of part[s][b]
 template <typename T>
-__global__ void k_scale_batch(int M, int N, T beta, T *C, int64_t ldc, int64_t sC, int batch) {
+__global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, const T *part, T beta, T *C, int64_t ldc,
+                                int64_t sC) {
   const int64_t per = (int64_t)M * N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per * batch;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t b = e / per, w = e % per;
+    T acc = T(0);
+    for (int s = 0; s < ksplit; ++s) acc += part[((int64_t)s * batch + b) * per + w];
     T *c = C + b * sC + (w % M) + (w / M) * ldc;
-    *c = (beta == T(0)) ? T(0) : beta * *c;
+    *c = acc + (beta == T(0) ? T(0) : beta * *c);
   }
 }
 
 template <typename T, int BM, int BN, int TM, int TN_>
 void launch_shape(bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda, int64_t sA, const T *B,
                   int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC, int batch, int ksplit,
-                  cudaStream_t st) {
+                  T *part, cudaStream_t st) {
   dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN), (unsigned)(batch * ksplit));
   constexpr int NT = (BM / TM) * (BN / TN_);
   note_launch();
   if (transA)
     k_gemm<T, BM, BN, TM, TN_, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                          sC, ksplit);
+                                                          sC, ksplit, part);
   else
     k_gemm<T, BM, BN, TM, TN_, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                           sC, ksplit);
+                                                           sC, ksplit, part);
 }
 
 }  // namespace
@@ -175,18 +185,20 @@ Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alp
     ksplit = (int)std::min<int64_t>(std::max<int64_t>(1, target / tiles), K / 128);
     ksplit = std::max(ksplit, 1);
   }
-  if (ksplit > 1 && beta != T(1)) {
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * N * batch, 256), 4096);
-    note_launch();
-    k_scale_batch<T><<<g, 256, 0, st>>>(M, N, beta, C, ldc, sC, batch);
-    beta = T(1);
-  }
+  T *part = nullptr;
+  if (ksplit > 1) CK_CUDA(cudaMallocAsync((void **)&part, sizeof(T) * (size_t)M * N * batch * ksplit, st));
   if (big)
     launch_shape<T, 128, 128, 8, 8>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
-                                    st);
+                                    part, st);
   else
     launch_shape<T, 64, 64, 4, 4>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
-                                  st);
+                                  part, st);
+  if (ksplit > 1) {
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * N * batch, 256), 4096);
+    note_launch();
+    k_splitk_reduce<T><<<g, 256, 0, st>>>(M, N, batch, ksplit, part, beta, C, ldc, sC);
+    cudaFreeAsync(part, st);
+  }
   CK_CUDA(cudaGetLastError());
   return ok();
 }

@@ -51,15 +51,27 @@ enum : int {
 };
 
 // ----------------------------------------------------------------------------- context
+// The last Omega drawn on a context; buffers only grow, so that a context whose capacity
+// was reserved up front never allocates inside a captured graph.
 struct OmegaCache {
   int64_t n = -1;
   int32_t d = -1;
   uint64_t seed = 0;
   uint32_t *bits = nullptr;     // ceil(n/32) words
+  size_t bits_cap = 0;          // words
   int32_t *cols = nullptr;      // d
+  size_t cols_cap = 0;
   __nv_bfloat16 *omegaT = nullptr;  // d x kpad, row j = Omega column j (unscaled +-1)
+  size_t omegaT_cap = 0;        // bytes
   int64_t kpad = 0;
-  size_t omegaT_bytes = 0;
+  bool omegaT_valid = false;
+};
+
+// Pinned host memory for descriptor uploads made while a stream is being captured: each
+// upload gets its own bytes, alive until the graph has run.
+struct UploadArena {
+  unsigned char *host = nullptr;
+  size_t cap = 0, used = 0;
 };
 
 }  // namespace ckinv
@@ -83,6 +95,8 @@ struct ckinv_ctx {
   uint32_t *cand_idx = nullptr;
   uint32_t *small = nullptr;          // small counters
   size_t cand_cap = 0;
+  // set while the context's work is being captured into a CUDA graph
+  ckinv::UploadArena *capture_arena = nullptr;
 };
 
 struct ckinv_factor {
@@ -136,6 +150,8 @@ Error stage_upload(ckinv_ctx *ctx, const void *src, size_t bytes, void *dst, cud
 // ----------------------------------------------------------------------------- Omega
 Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream_t st);
 Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st);   // ctx->om.omegaT
+// Grows the context's Omega buffers and draw scratch to hold an (n, d) draw (no draw).
+Error omega_reserve(ckinv_ctx *ctx, int64_t n, int32_t d, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- sketch
 Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp,

@@ -12,7 +12,8 @@ namespace {
 
 // ---------------------------------------------------------------- G = L^T M over n rows
 // Tile 64 x 64 of G per CTA, rows split over gridDim.z chunks; FP32 FMA inside 256-row
-// sub-chunks, FP64 accumulation across them, FP64 atomics into G (zeroed by the caller).
+// sub-chunks, FP64 accumulation across them; chunk z writes its partial product to
+// G + z d1 d2, and the partials are folded in chunk order afterwards (deterministic).
 template <bool OMEGA>
 __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const float *__restrict__ L,
                                                 int64_t ldl, const uint32_t *__restrict__ bits,
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
     for (int y = 0; y < 4; ++y) {
       int i = i0 + ty * 4 + x, j = j0 + tx * 4 + y;
       if (i < d1 && j < d2)
-        atomicAdd(&G[i + (int64_t)j * d1], (OMEGA ? oscale : 1.0) * (accd[x][y] + (double)acc[x][y]));
+        G[(int64_t)blockIdx.z * d1 * d2 + i + (int64_t)j * d1] = (OMEGA ? oscale : 1.0) * (accd[x][y] + (double)acc[x][y]);
     }
 }
 
@@ -99,7 +100,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &err) 
   err = (a - (s - bb)) + (b - bb);
 }
 
-// G (d1 x d2, FP64, ld d1) += L^T M over rows [rb, re) (L, M FP32), compensated.
+// Partial z of G (d1 x d2, FP64, ld d1) = L^T M over rows [rb, re) (L, M FP32), compensated.
 __global__ void __launch_bounds__(256) k_tsprod_dd(int64_t n, int d1, int d2, const float *__restrict__ L,
                                                    int64_t ldl, const float *__restrict__ M, int64_t ldm,
                                                    double *G, int64_t rows_per_split) {
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(256) k_tsprod_dd(int64_t n, int d1, int d2, co
 #pragma unroll
     for (int y = 0; y < 2; ++y) {
       int i = i0 + ty * 4 + x, j = j0 + tx * 2 + y;
-      if (i < d1 && j < d2) atomicAdd(&G[i + (int64_t)j * d1], acc[x][y] + (double)hs[x][y] + (double)lc[x][y]);
+      if (i < d1 && j < d2)
+        G[(int64_t)blockIdx.z * d1 * d2 + i + (int64_t)j * d1] = acc[x][y] + (double)hs[x][y] + (double)lc[x][y];
     }
 }
 
@@ -417,31 +419,50 @@ int splits_for(const ckinv_ctx *ctx, int64_t n, int tiles) {
 
 }  // namespace
 
+// G = sum over s (in order) of part[s]: the row splits of a product folded deterministically.
+__global__ void k_fold_splits(int64_t count, int splits, const double *part, double *G) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += part[(int64_t)s * count + e];
+    G[e] = acc;
+  }
+}
+
+static Error fold_splits(int64_t count, int splits, double *part, double *G, cudaStream_t st) {
+  ::ckinv::note_launch(), k_fold_splits<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 2048), 256, 0, st>>>(
+                              count, splits, part, G);
+  CK_CUDA(cudaGetLastError());
+  cudaFreeAsync(part, st);
+  return ok();
+}
+
 Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const uint32_t *bits,
              const int32_t *cols, double oscale, const float *M, int64_t ldm, double *G, cudaStream_t st) {
-  CK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)d1 * d2, st));
   int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 64);
   int sp = splits_for(ctx, n, tx * ty);
   int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
+  double *part = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
   dim3 grid(tx, ty, sp);
-  if (L) ::ckinv::note_launch(), k_tsprod<false><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, G, rps);
-  else ::ckinv::note_launch(), k_tsprod<true><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, G, rps);
+  if (L) ::ckinv::note_launch(), k_tsprod<false><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+  else ::ckinv::note_launch(), k_tsprod<true><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
   CK_CUDA(cudaGetLastError());
-  return ok();
+  return fold_splits((int64_t)d1 * d2, sp, part, G, st);
 }
 
 static Error tsprod_dd(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const float *M,
                        int64_t ldm, double *G, cudaStream_t st) {
-  CK_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)d1 * d2, st));
   int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 32);
   int sp = splits_for(ctx, n, tx * ty);
   int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
+  double *part = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
   dim3 grid(tx, ty, sp);
-  ::ckinv::note_launch(), k_tsprod_dd<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, G, rps);
+  ::ckinv::note_launch(), k_tsprod_dd<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, part, rps);
   CK_CUDA(cudaGetLastError());
-  return ok();
+  return fold_splits((int64_t)d1 * d2, sp, part, G, st);
 }
 
 // Blocked LU of nmat strided d x d matrices: panel (one CTA per matrix), TRSM, GEMM update.

@@ -167,17 +167,46 @@ __global__ void k_omegaT(int64_t n, int64_t kpad, int d, const uint32_t *bits,
 
 }  // namespace
 
+namespace {
+template <typename T>
+Error grow(T **p, size_t *cap, size_t need, cudaStream_t st) {
+  if (*p && *cap >= need) return ok();
+  if (*p) cudaFreeAsync(*p, st);
+  *p = nullptr;
+  *cap = 0;
+  CK_CUDA(cudaMallocAsync((void **)p, sizeof(T) * need, st));
+  *cap = need;
+  return ok();
+}
+}  // namespace
+
+Error omega_reserve(ckinv_ctx *ctx, int64_t n, int32_t d, cudaStream_t st) {
+  OmegaCache &om = ctx->om;
+  CK_TRY(grow(&om.bits, &om.bits_cap, (size_t)ceil_div(n, 32), st));
+  CK_TRY(grow(&om.cols, &om.cols_cap, (size_t)d, st));
+  const int64_t kpad = ceil_div(n, 64) * 64;
+  size_t cap = om.omegaT_cap / sizeof(__nv_bfloat16);
+  CK_TRY(grow(&om.omegaT, &cap, (size_t)kpad * d, st));
+  om.omegaT_cap = cap * sizeof(__nv_bfloat16);
+  if (!ctx->hist) {
+    CK_CUDA(cudaMalloc((void **)&ctx->hist, sizeof(uint32_t) * 65536));
+    CK_CUDA(cudaMalloc((void **)&ctx->small, sizeof(uint32_t) * 16));
+    ctx->cand_cap = kSortCap;
+    CK_CUDA(cudaMalloc((void **)&ctx->cand, sizeof(unsigned long long) * ctx->cand_cap));
+    CK_CUDA(cudaMalloc((void **)&ctx->cand_idx, sizeof(uint32_t) * ctx->cand_cap));
+  }
+  return ok();
+}
+
 Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream_t st) {
   OmegaCache &om = ctx->om;
   if (om.n == n && om.d == d && om.seed == seed && om.bits) return ok();
   int64_t N = padded_order(n);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  if (om.bits) { cudaFreeAsync(om.bits, st); om.bits = nullptr; }
-  if (om.cols) { cudaFreeAsync(om.cols, st); om.cols = nullptr; }
-  if (om.omegaT) { cudaFreeAsync(om.omegaT, st); om.omegaT = nullptr; om.omegaT_bytes = 0; }
   om.n = -1;
-  CK_CUDA(cudaMallocAsync((void **)&om.bits, sizeof(uint32_t) * ceil_div(n, 32), st));
-  CK_CUDA(cudaMallocAsync((void **)&om.cols, sizeof(int32_t) * d, st));
+  om.omegaT_valid = false;
+  CK_TRY(grow(&om.bits, &om.bits_cap, (size_t)ceil_div(n, 32), st));
+  CK_TRY(grow(&om.cols, &om.cols_cap, (size_t)d, st));
   if (!ctx->hist) {
     CK_CUDA(cudaMalloc((void **)&ctx->hist, sizeof(uint32_t) * 65536));
     CK_CUDA(cudaMalloc((void **)&ctx->small, sizeof(uint32_t) * 16));
@@ -204,17 +233,16 @@ Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream
 
 Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st) {
   OmegaCache &om = ctx->om;
+  if (om.omegaT_valid) return ok();
   int64_t kpad = ceil_div(om.n, 64) * 64;
-  size_t bytes = sizeof(__nv_bfloat16) * (size_t)kpad * om.d;
-  if (om.omegaT && om.omegaT_bytes == bytes && om.kpad == kpad) return ok();
-  if (om.omegaT) cudaFreeAsync(om.omegaT, st);
-  om.omegaT = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&om.omegaT, bytes, st));
-  om.omegaT_bytes = bytes;
+  size_t cap = om.omegaT_cap / sizeof(__nv_bfloat16);
+  CK_TRY(grow(&om.omegaT, &cap, (size_t)kpad * om.d, st));
+  om.omegaT_cap = cap * sizeof(__nv_bfloat16);
   om.kpad = kpad;
   dim3 grid((unsigned)ceil_div(kpad / 2, 256), (unsigned)om.d);
   ::ckinv::note_launch(), k_omegaT<<<grid, 256, 0, st>>>(om.n, kpad, om.d, om.bits, om.cols, om.omegaT);
   CK_CUDA(cudaGetLastError());
+  om.omegaT_valid = true;
   return ok();
 }
 
