@@ -218,63 +218,90 @@ __global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, co
 
 // ---------------------------------------------------------------- LU (FP64, blocked)
 // Panel step of a right-looking blocked LU with partial pivoting on nmat strided d x d
-// matrices (ld d): columns k0 .. k0+kb-1 of matrix blockIdx.x are factored (pivot search,
-// full-row interchange, scaling, rank-1 updates inside the panel); piv[j] is the LAPACK
-// interchange and logabs[m] accumulates log|U_jj|.
-__global__ void __launch_bounds__(256) k_lu_panel(int d, int k0, int kb, double *A0, int32_t *piv0, double *logabs,
-                                                  int *err) {
-  __shared__ double sval[256];
-  __shared__ int sidx[256];
+// matrices (ld d): rows k0 .. d-1 of columns k0 .. k0+kb-1 of matrix blockIdx.x are
+// loaded into shared memory and factored there (pivot search, interchange within the
+// panel, scaling, rank-1 updates); piv[j] is the LAPACK interchange and logabs[m]
+// accumulates log|U_jj|.  The interchanges are applied to the other columns afterwards
+// (k_lu_laswp).
+constexpr int kLuPanelThreads = 512;
+__global__ void __launch_bounds__(kLuPanelThreads) k_lu_panel(int d, int k0, int kb, double *A0, int32_t *piv0,
+                                                              double *logabs, int *err) {
+  extern __shared__ double P[];          // (d - k0) x kb, ld R
+  __shared__ double wval[kLuPanelThreads / 32];
+  __shared__ int widx[kLuPanelThreads / 32];
+  __shared__ int s_p;
   const int m = blockIdx.x;
   double *A = A0 + (int64_t)m * d * d;
   int32_t *piv = piv0 + (int64_t)m * d;
-  const int tid = threadIdx.x;
+  const int R = d - k0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = 0; c < kb; ++c)
+    for (int i = tid; i < R; i += blockDim.x) P[i + c * R] = A[(k0 + i) + (int64_t)(k0 + c) * d];
+  __syncthreads();
   double la = 0.0;
-  for (int j = k0; j < k0 + kb; ++j) {
+  for (int j = 0; j < kb; ++j) {
+    // pivot: largest |P[i, j]| over i >= j, ties to the smaller row
     double best = -1.0;
     int bi = j;
-    for (int i = j + tid; i < d; i += 256) {
-      double v = fabs(A[i + (int64_t)j * d]);
+    for (int i = j + tid; i < R; i += blockDim.x) {
+      double v = fabs(P[i + j * R]);
       if (v > best) { best = v; bi = i; }
     }
-    sval[tid] = best;
-    sidx[tid] = bi;
-    __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-      if (tid < off) {
-        double o = sval[tid + off];
-        int oi = sidx[tid + off];
-        if (o > sval[tid] || (o == sval[tid] && oi < sidx[tid])) { sval[tid] = o; sidx[tid] = oi; }
-      }
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    const int p = sidx[0];
-    if (p != j)
-      for (int c = tid; c < d; c += 256) {
-        double t = A[j + (int64_t)c * d];
-        A[j + (int64_t)c * d] = A[p + (int64_t)c * d];
-        A[p + (int64_t)c * d] = t;
-      }
+    if (lane == 0) { wval[wid] = best; widx[wid] = bi; }
     __syncthreads();
-    const double pv = A[j + (int64_t)j * d];
     if (tid == 0) {
-      piv[j] = p;
+      double bv = wval[0];
+      int bj = widx[0];
+      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+        if (wval[w] > bv || (wval[w] == bv && widx[w] < bj)) { bv = wval[w]; bj = widx[w]; }
+      s_p = bj;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j && tid < kb) {
+      double t = P[j + tid * R];
+      P[j + tid * R] = P[p + tid * R];
+      P[p + tid * R] = t;
+    }
+    __syncthreads();
+    const double pv = P[j + j * R];
+    if (tid == 0) {
+      piv[k0 + j] = k0 + p;
       if (pv == 0.0) atomicOr(err, DERR_SINGULAR);
       else la += log(fabs(pv));
     }
     const double inv = (pv != 0.0) ? 1.0 / pv : 0.0;
-    for (int i = j + 1 + tid; i < d; i += 256) A[i + (int64_t)j * d] *= inv;
+    for (int i = j + 1 + tid; i < R; i += blockDim.x) P[i + j * R] *= inv;
     __syncthreads();
-    // rank-1 update of the rest of the panel
-    const int ncol = k0 + kb - j - 1;
-    const int nrow = d - j - 1;
-    for (int e = tid; e < ncol * nrow; e += 256) {
-      int i = j + 1 + e % nrow, c = j + 1 + e / nrow;
-      A[i + (int64_t)c * d] -= A[i + (int64_t)j * d] * A[j + (int64_t)c * d];
+    for (int i = j + 1 + tid; i < R; i += blockDim.x) {   // rank-1 update of the rest of the panel
+      const double l = P[i + j * R];
+      for (int c = j + 1; c < kb; ++c) P[i + c * R] = fma(-l, P[j + c * R], P[i + c * R]);
     }
     __syncthreads();
   }
+  for (int c = 0; c < kb; ++c)
+    for (int i = tid; i < R; i += blockDim.x) A[(k0 + i) + (int64_t)(k0 + c) * d] = P[i + c * R];
   if (tid == 0) logabs[m] += la;
+}
+
+// The panel's interchanges (rows k0 .. k0+kb-1) applied to every column outside the panel.
+__global__ void k_lu_laswp(int d, int k0, int kb, double *A0, const int32_t *piv0) {
+  double *A = A0 + (int64_t)blockIdx.y * d * d;
+  const int32_t *piv = piv0 + (int64_t)blockIdx.y * d;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d - kb) return;
+  if (c >= k0) c += kb;                  // skip the panel's own columns
+  double *col = A + (int64_t)c * d;
+  for (int j = k0; j < k0 + kb; ++j) {
+    int p = piv[j];
+    if (p != j) { double t = col[j]; col[j] = col[p]; col[p] = t; }
+  }
 }
 
 // A[k0:k0+kb, k0+kb:d] <- L11^-1 A[k0:k0+kb, k0+kb:d]  (L11 unit lower), one thread per column.
@@ -291,56 +318,147 @@ __global__ void k_lu_trsm(int d, int k0, int kb, double *A0) {
 }
 
 // ---------------------------------------------------------------- triangular solves
-// X (d x m, ld d) <- op(A)^-1 X with A = P L U packed (LAPACK interchanges).  One CTA per
-// right-hand side; column-oriented substitution (no reductions).
-__global__ void k_lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans) {
-  extern __shared__ double xs[];
-  const int c = blockIdx.x;
-  if (c >= m) return;
-  double *x = X + (int64_t)c * d;
-  for (int i = threadIdx.x; i < d; i += blockDim.x) xs[i] = x[i];
-  __syncthreads();
-  if (!trans) {
-    if (threadIdx.x == 0)
-      for (int j = 0; j < d; ++j) {
-        int p = piv[j];
-        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
-      }
+// X (d x m, ld d) <- op(A)^-1 X with A = P L U packed (LAPACK interchanges), d <= 512.
+// One warp per right-hand side, its vector in registers (element i in lane i % 32, slot
+// i / 32), kSolveWarps right-hand sides per block sharing the factor: the columns of L
+// and U are staged through shared memory kSolveChunk at a time by the whole block, so a
+// step costs a shared-memory read and a shuffle, not an L2 round trip.  L and U are
+// applied by columns; U^T and L^T in dot-product form (a column per step, then a warp
+// sum).  The interchanges go through a per-warp shared-memory copy of the vector.
+constexpr int kSolveSlots = 16;
+constexpr int kSolveWarps = 8;
+constexpr int kSolveChunk = 16;
+__device__ __forceinline__ double slot_get(const double (&v)[kSolveSlots], int s) {
+  double r = 0.0;
+#pragma unroll
+  for (int t = 0; t < kSolveSlots; ++t) r = (t == s) ? v[t] : r;
+  return r;
+}
+__device__ __forceinline__ void slot_set(double (&v)[kSolveSlots], int s, double x) {
+#pragma unroll
+  for (int t = 0; t < kSolveSlots; ++t) v[t] = (t == s) ? x : v[t];
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(32 * kSolveWarps) k_lu_solve(int d, int m, const double *__restrict__ LU,
+                                                               const int32_t *__restrict__ piv, double *X,
+                                                               int trans) {
+  extern __shared__ double sm[];
+  double *cols = sm;                                   // kSolveChunk columns, ld d
+  double *xs = sm + (size_t)kSolveChunk * d + (size_t)(threadIdx.x >> 5) * d;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kSolveWarps + (threadIdx.x >> 5);
+  const bool active = c < m;                           // idle warps still stage columns
+  double *x = X + (int64_t)(active ? c : 0) * d;
+  double v[kSolveSlots];
+  const int nchunk = (d + kSolveChunk - 1) / kSolveChunk;
+  // stage columns [j0, j0 + kSolveChunk) of LU
+  auto stage = [&](int ch) {
     __syncthreads();
-    for (int j = 0; j < d; ++j) {          // L y = P x  (unit lower)
-      double xj = xs[j];
-      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) xs[i] -= LU[i + (int64_t)j * d] * xj;
-      __syncthreads();
+    const int j0 = ch * kSolveChunk;
+    const int w = min(kSolveChunk, d - j0);
+    for (int e = threadIdx.x; e < w * d; e += blockDim.x) cols[e] = LU[(int64_t)j0 * d + e];
+    __syncthreads();
+  };
+  auto swaps = [&](bool forward) {
+    if (lane == 0 && active) {
+      if (forward) {
+        for (int j = 0; j < d; ++j) {
+          int p = piv[j];
+          if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+        }
+      } else {
+        for (int j = d - 1; j >= 0; --j) {
+          int p = piv[j];
+          if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+        }
+      }
     }
-    for (int j = d - 1; j >= 0; --j) {     // U x = y
-      if (threadIdx.x == 0) xs[j] /= LU[j + (int64_t)j * d];
-      __syncthreads();
-      double xj = xs[j];
-      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= LU[i + (int64_t)j * d] * xj;
-      __syncthreads();
+    __syncwarp();
+  };
+  if (!trans) {
+    if (active) for (int i = lane; i < d; i += 32) xs[i] = x[i];
+    __syncwarp();
+    swaps(true);
+#pragma unroll
+    for (int s = 0; s < kSolveSlots; ++s) v[s] = (s * 32 + lane < d) ? xs[s * 32 + lane] : 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) {            // L y = P x  (unit lower), by columns
+      stage(ch);
+      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
+      for (int j = j0; j < j1; ++j) {
+        const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31);
+        const double *col = cols + (size_t)(j - j0) * d;
+#pragma unroll
+        for (int s = 0; s < kSolveSlots; ++s) {
+          const int i = s * 32 + lane;
+          if (i > j && i < d) v[s] = fma(-col[i], xj, v[s]);
+        }
+      }
+    }
+    for (int ch = nchunk - 1; ch >= 0; --ch) {       // U x = y, by columns
+      stage(ch);
+      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
+      for (int j = j1 - 1; j >= j0; --j) {
+        const double *col = cols + (size_t)(j - j0) * d;
+        const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31) / col[j];
+        if (lane == (j & 31)) slot_set(v, j >> 5, xj);
+#pragma unroll
+        for (int s = 0; s < kSolveSlots; ++s) {
+          const int i = s * 32 + lane;
+          if (i < j) v[s] = fma(-col[i], xj, v[s]);
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < kSolveSlots; ++s)
+        if (s * 32 + lane < d) x[s * 32 + lane] = v[s];
     }
   } else {
     // A^T = U^T L^T P:  U^T z = x (lower), L^T w = z (unit upper), x = P^T w
-    for (int j = 0; j < d; ++j) {
-      if (threadIdx.x == 0) xs[j] /= LU[j + (int64_t)j * d];
-      __syncthreads();
-      double xj = xs[j];
-      for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) xs[i] -= LU[j + (int64_t)i * d] * xj;
-      __syncthreads();
-    }
-    for (int j = d - 1; j >= 0; --j) {
-      double xj = xs[j];
-      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] -= LU[j + (int64_t)i * d] * xj;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0)
-      for (int j = d - 1; j >= 0; --j) {
-        int p = piv[j];
-        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+#pragma unroll
+    for (int s = 0; s < kSolveSlots; ++s) v[s] = (active && s * 32 + lane < d) ? x[s * 32 + lane] : 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) {            // z_j = (x_j - sum_{i<j} U_ij z_i) / U_jj
+      stage(ch);
+      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
+      for (int j = j0; j < j1; ++j) {
+        const double *col = cols + (size_t)(j - j0) * d;
+        double part = 0.0;
+#pragma unroll
+        for (int s = 0; s < kSolveSlots; ++s) {
+          const int i = s * 32 + lane;
+          if (i < j) part = fma(col[i], v[s], part);
+        }
+        const double tot = warp_sum(part);
+        if (lane == (j & 31)) slot_set(v, j >> 5, (slot_get(v, j >> 5) - tot) / col[j]);
       }
-    __syncthreads();
+    }
+    for (int ch = nchunk - 1; ch >= 0; --ch) {       // w_j = z_j - sum_{i>j} L_ij w_i
+      stage(ch);
+      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
+      for (int j = j1 - 1; j >= j0; --j) {
+        const double *col = cols + (size_t)(j - j0) * d;
+        double part = 0.0;
+#pragma unroll
+        for (int s = 0; s < kSolveSlots; ++s) {
+          const int i = s * 32 + lane;
+          if (i > j && i < d) part = fma(col[i], v[s], part);
+        }
+        const double tot = warp_sum(part);
+        if (lane == (j & 31)) slot_set(v, j >> 5, slot_get(v, j >> 5) - tot);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kSolveSlots; ++s)
+      if (s * 32 + lane < d) xs[s * 32 + lane] = v[s];
+    __syncwarp();
+    swaps(false);
+    if (active) for (int i = lane; i < d; i += 32) x[i] = xs[i];
   }
-  for (int i = threadIdx.x; i < d; i += blockDim.x) x[i] = xs[i];
 }
 
 // C (d x m) = op(A) (d x d) * Bm (d x m), FP64, ld = d.  transA: C = A^T B.
@@ -470,11 +588,19 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
   constexpr int NBL = 32;
   CK_CUDA(cudaMemsetAsync(logabs, 0, sizeof(double) * nmat, st));
   const int64_t sA = (int64_t)d * d;
+  const size_t smem_max = sizeof(double) * (size_t)d * NBL;
+  CK_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   for (int k0 = 0; k0 < d; k0 += NBL) {
     const int kb = std::min(NBL, d - k0);
     note_launch();
-    k_lu_panel<<<nmat, 256, 0, st>>>(d, k0, kb, A, piv, logabs, ctx->d_err);
+    k_lu_panel<<<nmat, kLuPanelThreads, sizeof(double) * (size_t)(d - k0) * kb, st>>>(d, k0, kb, A, piv, logabs,
+                                                                                      ctx->d_err);
     CK_CUDA(cudaGetLastError());
+    if (d > kb) {
+      note_launch();
+      k_lu_laswp<<<dim3((unsigned)ceil_div(d - kb, 128), nmat), 128, 0, st>>>(d, k0, kb, A, piv);
+      CK_CUDA(cudaGetLastError());
+    }
     const int rest = d - k0 - kb;
     if (rest <= 0) continue;
     note_launch();
@@ -489,7 +615,12 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
 }
 
 static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
-  ::ckinv::note_launch(), k_lu_solve<<<m, 256, sizeof(double) * d, st>>>(d, m, LU, piv, X, trans);
+  if (d > 32 * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
+  const size_t smem = sizeof(double) * (size_t)(kSolveChunk + kSolveWarps) * d;
+  CK_CUDA(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(double) * (kSolveChunk + kSolveWarps) * 512)));
+  ::ckinv::note_launch(), k_lu_solve<<<(unsigned)ceil_div(m, kSolveWarps), 32 * kSolveWarps, smem, st>>>(d, m, LU, piv,
+                                                                                                       X, trans);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
