@@ -270,6 +270,104 @@ Error axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta
   return ok();
 }
 
+// ---------------------------------------------------------------- tree combine panels
+// Householder QR of stacked pairs S = [R_a; R_b] (2d x d, ld 2d, both blocks upper
+// triangular) in panels of sq_nb(T) columns.  Reflector j is e_j on top and v_j (rows
+// 0..j) below, so only the top row j and the bottom rows 0..j take part.  One CTA per
+// combine factors a panel in shared memory (k_sq_panel: every dot product of a step in one
+// pass, one warp per column); the trailing columns and the off-diagonal blocks of the
+// compact-WY factor T are batched GEMMs over all combines of the level (sq_factor).
+template <typename T>
+constexpr int sq_nb() { return sizeof(T) == 4 ? 32 : 16; }
+constexpr int SQ_THREADS = 256;
+
+template <typename T>
+size_t sq_panel_smem(int d) {
+  constexpr int NBS = sq_nb<T>();
+  return sizeof(T) * ((size_t)d * NBS + 2 * NBS * NBS + NBS + 4);
+}
+
+// Panel [j0, j0 + nb) of every combine: R rows into the top of S, V_bot columns into rows
+// d..2d-1 of Vx (zeros below each reflector), the panel's T block into Tm's diagonal.
+template <typename T>
+__global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, int d, int j0) {
+  constexpr int NBS = sq_nb<T>();
+  constexpr int NW = SQ_THREADS / 32;
+  extern __shared__ __align__(16) uint8_t sm_raw[];
+  T *Vp = reinterpret_cast<T *>(sm_raw);          // NBS columns x d rows: the panel's bottom part
+  T *Ct = Vp + (size_t)NBS * d;                   // NBS x NBS top block, row-major
+  T *Tk = Ct + NBS * NBS;                         // NBS x NBS panel T, row-major
+  T *Dt = Tk + NBS * NBS;                         // NBS raw dots of the current step
+  const int H = 2 * d;
+  T *M = M0 + (int64_t)blockIdx.x * H * d;
+  T *Vx = Vx0 + (int64_t)blockIdx.x * H * d;
+  T *Tm = Tm0 + (int64_t)blockIdx.x * d * d;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = min(NBS, d - j0);
+  const int rows = j0 + nb;                       // bottom rows the panel touches
+  for (int c = 0; c < nb; ++c)
+    for (int i = tid; i < rows; i += SQ_THREADS) Vp[c * d + i] = M[d + i + (int64_t)(j0 + c) * H];
+  for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
+    const int r = e / NBS, c = e % NBS;
+    Ct[e] = (r < nb && c < nb) ? M[j0 + r + (int64_t)(j0 + c) * H] : T(0);
+    Tk[e] = T(0);
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nb; ++jj) {
+    const int j = j0 + jj;                        // bottom rows 0..j are active
+    const T *x = Vp + jj * d;
+    // raw dots of x with every panel column (c == jj gives |x|^2), one warp per column
+    for (int c = wid; c < nb; c += NW) {
+      const T *y = Vp + c * d;
+      T acc = 0;
+      for (int i = lane; i <= j; i += 32) acc += x[i] * y[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Dt[c] = acc;
+    }
+    __syncthreads();
+    const T alpha = Ct[jj * NBS + jj];
+    const T sig = Dt[jj];
+    const T normx = sqrt(alpha * alpha + sig);
+    T tau = 0, rd = alpha, inv_head = 0;
+    if (normx > T(0) && sig > T(0)) {
+      const T sgn = alpha >= T(0) ? T(1) : T(-1);
+      const T head = alpha + sgn * normx;
+      inv_head = T(1) / head;
+      tau = T(2) / (T(1) + sig * inv_head * inv_head);
+      rd = -sgn * normx;
+    }
+    // the rest of the panel: w_c = Ct[jj][c] + (x . col_c) / head, then the reflection
+    for (int c = jj + 1 + wid; c < nb; c += NW) {
+      const T w = tau * (Ct[jj * NBS + c] + Dt[c] * inv_head);
+      T *col = Vp + c * d;
+      for (int i = lane; i <= j; i += 32) col[i] -= w * x[i] * inv_head;
+      if (lane == 0) Ct[jj * NBS + c] -= w;
+    }
+    // T within the panel: T[r][jj] = -tau sum_{l=r}^{jj-1} T[r][l] (v_l . v_jj)
+    if (tid < jj) {
+      T acc = 0;
+      for (int l = tid; l < jj; ++l) acc += Tk[tid * NBS + l] * (Dt[l] * inv_head);
+      Tk[tid * NBS + jj] = -tau * acc;
+    }
+    __syncthreads();
+    for (int i = tid; i <= j; i += SQ_THREADS) Vp[jj * d + i] = x[i] * inv_head;
+    if (tid == 0) {
+      Ct[jj * NBS + jj] = rd;
+      Tk[jj * NBS + jj] = tau;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += SQ_THREADS) {
+    const int r = e / nb, c = e % nb;
+    M[j0 + r + (int64_t)(j0 + c) * H] = (r <= c) ? Ct[r * NBS + c] : T(0);
+    Tm[(j0 + r) + (int64_t)(j0 + c) * d] = Tk[r * NBS + c];
+  }
+  for (int c = 0; c < nb; ++c)
+    for (int i = tid; i < d; i += SQ_THREADS)
+      Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] : T(0);
+}
+
 // One stage: P independent QRs of H x d matrices (strided, ld H).
 template <typename T>
 struct Stage {
@@ -403,8 +501,63 @@ Error alloc_stage(Stage<T> &s, int P, int H, int d, const std::vector<int> &top,
   return ok();
 }
 
+// Panel by panel over all combines of a level: the panel kernel, then
+//   T[0:j0, panel] = -T[0:j0, 0:j0] (V_bot[:, 0:j0]^T V_panel) T_panel,
+//   W = C_top + V_panel^T C_bot,  W2 = T_panel^T W,  C_top -= W2,  C_bot -= V_panel W2
+// on the trailing columns (rows 0..j0+nb-1 of the bottom block).
+template <typename T>
+Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st) {
+  constexpr int NBS = sq_nb<T>();
+  const int H = s.H, P = s.P;
+  const int64_t sM = (int64_t)H * d, sT = (int64_t)d * d, sW = (int64_t)NBS * d;
+  const size_t smem = sq_panel_smem<T>(d);
+  CK_CUDA(cudaFuncSetAttribute(k_sq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  T *W = nullptr, *W2 = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * (size_t)P * sW, st));
+  CK_CUDA(cudaMallocAsync((void **)&W2, sizeof(T) * (size_t)P * sW, st));
+  Error e = ok();
+  for (int j0 = 0; j0 < d && !e.st; j0 += NBS) {
+    const int nb = std::min(NBS, d - j0), rows = j0 + nb, nt = d - rows;
+    note_launch();
+    k_sq_panel<T><<<P, SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, d, j0);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { e = fail(CKINV_ECUDA, cudaGetErrorString(ce)); break; }
+    T *Vb = s.Vx + d;                          // V_bot, ld H
+    T *Vpan = Vb + (int64_t)j0 * H;
+    T *Tkk = s.Tm + j0 + (int64_t)j0 * d;
+    if (j0 > 0) {
+      // S (j0 x nb, ld j0) = V_bot[0:rows, 0:j0]^T V_panel ; U = T11 S ; T12 = -U T_kk
+      if ((e = gemm_batched<T>(ctx, true, j0, nb, rows, T(1), Vb, H, sM, Vpan, H, sM, T(0), W, j0, sW, P, st)).st) break;
+      if ((e = gemm_batched<T>(ctx, false, j0, nb, j0, T(1), s.Tm, d, sT, W, j0, sW, T(0), W2, j0, sW, P, st)).st) break;
+      if ((e = gemm_batched<T>(ctx, false, j0, nb, nb, T(-1), W2, j0, sW, Tkk, d, sT, T(0), s.Tm + (int64_t)j0 * d, d,
+                               sT, P, st)).st)
+        break;
+    }
+    if (nt > 0) {
+      T *Ct = s.M + j0 + (int64_t)rows * H;    // top rows of the panel, trailing columns
+      T *Cb = s.M + d + (int64_t)rows * H;     // bottom rows 0..rows-1, trailing columns
+      if ((e = axpby<T>(nb, nt, T(1), Ct, H, sM, T(0), W, nb, sW, P, st)).st) break;
+      if ((e = gemm_batched<T>(ctx, true, nb, nt, rows, T(1), Vpan, H, sM, Cb, H, sM, T(1), W, nb, sW, P, st)).st) break;
+      if ((e = gemm_batched<T>(ctx, true, nb, nt, nb, T(1), Tkk, d, sT, W, nb, sW, T(0), W2, nb, sW, P, st)).st) break;
+      if ((e = axpby<T>(nb, nt, T(-1), W2, nb, sW, T(1), Ct, H, sM, P, st)).st) break;
+      if ((e = gemm_batched<T>(ctx, false, rows, nt, nb, T(-1), Vpan, H, sM, W2, nb, sW, T(1), Cb, H, sM, P, st)).st) break;
+    }
+  }
+  cudaFreeAsync(W, st);
+  cudaFreeAsync(W2, st);
+  return e;
+}
+
 template <typename T>
 Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot, cudaStream_t st) {
+  if (s.stacked) {
+    CK_TRY(sq_factor<T>(ctx, s, d, st));
+    dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 64), s.P);
+    note_launch();
+    k_extract_r<T><<<g, 256, 0, st>>>(s.M, s.H, d, s.top, Rslot);
+    CK_CUDA(cudaGetLastError());
+    return ok();
+  }
   T *W = nullptr, *W2 = nullptr;
   const size_t sw = (size_t)s.P * ((d / 2 + NB) * (d / 2 + NB));
   CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * sw, st));
