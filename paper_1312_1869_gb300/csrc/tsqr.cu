@@ -163,10 +163,10 @@ __global__ void k_gather_leaves(const float *Y, int64_t ldy, const int64_t *row0
   const int64_t r0 = row0[p];
   const int h = rows[p];
   T *dst = M + (int64_t)p * H * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)H * d;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % H), c = (int)(e / H);
-    dst[e] = (r < h) ? (T)Y[r0 + r + (int64_t)c * ldy] : T(0);
+  for (int c = blockIdx.x; c < d; c += gridDim.x) {
+    const float *src = Y + r0 + (int64_t)c * ldy;
+    T *out = dst + (int64_t)c * H;
+    for (int r = threadIdx.x; r < H; r += blockDim.x) out[r] = (r < h) ? (T)src[r] : T(0);
   }
 }
 
@@ -211,10 +211,9 @@ __global__ void k_init_qs(const double *Xslot, const int *top, int H, int d, T *
   const int p = blockIdx.y;
   const double *x = Xslot + (int64_t)top[p] * d * d;
   T *dst = Qs + (int64_t)p * H * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)H * d;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % H), c = (int)(e / H);
-    dst[e] = (r < d) ? (T)x[r + (int64_t)c * d] : T(0);
+  for (int c = blockIdx.x; c < d; c += gridDim.x) {
+    T *out = dst + (int64_t)c * H;
+    for (int r = threadIdx.x; r < H; r += blockDim.x) out[r] = (r < d) ? (T)x[r + (int64_t)c * d] : T(0);
   }
 }
 
@@ -238,10 +237,10 @@ __global__ void k_leaf_q(const T *Qs, int H, int d, const int64_t *row0, const i
   const int p = blockIdx.y;
   const int h = rows[p];
   const T *src = Qs + (int64_t)p * H * d;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)h * d;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % h), c = (int)(e / h);
-    Q[row0[p] + r + (int64_t)c * ldq] = (float)src[r + (int64_t)c * H];
+  for (int c = blockIdx.x; c < d; c += gridDim.x) {
+    const T *in = src + (int64_t)c * H;
+    float *out = Q + row0[p] + (int64_t)c * ldq;
+    for (int r = threadIdx.x; r < h; r += blockDim.x) out[r] = (float)in[r];
   }
 }
 
@@ -456,7 +455,7 @@ Error apply_q(const ckinv_ctx *ctx, const Stage<T> &s, int d, const double *Xslo
               cudaStream_t st) {
   const int H = s.H, P = s.P;
   const int64_t sM = (int64_t)H * d, sD = (int64_t)d * d;
-  dim3 g((unsigned)std::min<int64_t>(ceil_div(sM, 256), 256), P);
+  dim3 g((unsigned)std::min(d, 128), P);
   note_launch();
   k_init_qs<T><<<g, 256, 0, st>>>(Xslot, s.top, H, d, Qs);
   CK_CUDA(cudaGetLastError());
@@ -467,6 +466,7 @@ Error apply_q(const ckinv_ctx *ctx, const Stage<T> &s, int d, const double *Xslo
     CK_TRY(gemm_batched<T>(ctx, false, d, d, d, T(-1), s.Vx + d, H, sM, Z2, d, sD, T(0), Qs + d, H, sM, P, st));
     return ok();
   }
+  // V^T [X; 0] = V[0:d]^T X: the zero rows of [X; 0] contribute nothing
   CK_TRY(gemm_batched<T>(ctx, true, d, d, d, T(1), s.Vx, H, sM, Qs, H, sM, T(0), Z1, d, sD, P, st));
   CK_TRY(gemm_batched<T>(ctx, false, d, d, d, T(1), s.Tm, d, sD, Z1, d, sD, T(0), Z2, d, sD, P, st));
   CK_TRY(gemm_batched<T>(ctx, false, H, d, d, T(-1), s.Vx, H, sM, Z2, d, sD, T(1), Qs, H, sM, P, st));
@@ -641,7 +641,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     for (int i = 0; i < L; ++i) ident[i] = i;
     if ((e = alloc_stage<TL>(leaf, L, Hl, d, ident, {}, ctx, owned, st)).st) break;
     {
-      dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)Hl * d, 256), 512), L);
+      dim3 g((unsigned)std::min(d, 128), L);
       note_launch();
       k_gather_leaves<TL><<<g, 256, 0, st>>>(Y, ldy, d_row0, d_rows, Hl, d, leaf.M);
     }
@@ -699,7 +699,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     if (e.st) break;
     if ((e = apply_q<TL>(ctx, leaf, d, Xslot, (TL *)Qs, (TL *)Z1, (TL *)Z2, st)).st) break;
     {
-      dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)Hl * d, 256), 512), L);
+      dim3 g((unsigned)std::min(d, 128), L);
       note_launch();
       k_leaf_q<TL><<<g, 256, 0, st>>>((TL *)Qs, Hl, d, d_row0, d_rows, Qout, n);
     }
