@@ -662,6 +662,16 @@ ckinv_status ckinv_create(ckinv_ctx **out, int device) {
   ckinv_ctx *ctx = new ckinv_ctx();
   ctx->device = device;
   ctx->sm_count = prop.multiProcessorCount;
+  // Keep memory freed with cudaFreeAsync in the device's pool instead of returning it at
+  // every synchronisation: the library's stream-ordered workspaces (hundreds of MB per solve)
+  // are then reused without remapping.  A per-process allocator setting.
+  {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   if (cudaMalloc((void **)&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
     delete ctx;
     return finish(nullptr, fail(CKINV_ENOMEM, "context allocation failed"));
