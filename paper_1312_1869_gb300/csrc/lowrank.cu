@@ -11,24 +11,26 @@ namespace ckinv {
 namespace {
 
 // ---------------------------------------------------------------- G = L^T M over n rows
-// Tile 64 x 64 of G per CTA, rows split over gridDim.z chunks; FP32 FMA inside 256-row
-// sub-chunks, FP64 accumulation across them; chunk z writes its partial product to
-// G + z d1 d2, and the partials are folded in chunk order afterwards (deterministic).
-template <bool OMEGA>
+// Tile TM x TN of G per CTA (64 x 64, or 128 x 32 for a narrow right factor), rows split
+// over gridDim.z chunks; FP32 FMA inside 256-row sub-chunks, FP64 accumulation across them;
+// chunk z writes its partial product to G + z d1 d2, and the partials are folded in chunk
+// order afterwards (deterministic).
+template <bool OMEGA, int TM, int TN>
 __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const float *__restrict__ L,
                                                 int64_t ldl, const uint32_t *__restrict__ bits,
                                                 const int32_t *__restrict__ cols, double oscale,
                                                 const float *__restrict__ M, int64_t ldm, double *G,
                                                 int64_t rows_per_split) {
-  __shared__ float Ls[32][64 + 4];
-  __shared__ float Ms[32][64 + 4];
-  __shared__ uint32_t pc[64];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  static_assert((TM / 4) * (TN / 4) == 256, "4 x 4 outputs per thread");
+  __shared__ float Ls[32][TM + 4];
+  __shared__ float Ms[32][TN + 4];
+  __shared__ uint32_t pc[TM];
+  const int tid = threadIdx.x, tx = tid % (TN / 4), ty = tid / (TN / 4);
+  const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
   const int64_t rb = (int64_t)blockIdx.z * rows_per_split;
   const int64_t re = min(n, rb + rows_per_split);
   if (OMEGA)
-    for (int c = tid; c < 64; c += 256) pc[c] = (i0 + c < d1) ? (uint32_t)cols[i0 + c] : 0u;
+    for (int c = tid; c < TM; c += 256) pc[c] = (i0 + c < d1) ? (uint32_t)cols[i0 + c] : 0u;
   float acc[4][4];
   double accd[4][4];
 #pragma unroll
@@ -39,25 +41,28 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
   int step = 0;
   for (int64_t k0 = rb; k0 < re; k0 += 32) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < TM / 8; ++q) {
       int e = tid + 256 * q;
       int kk = e % 32, c = e / 32;
       int64_t k = k0 + kk;
-      float lv = 0.f, mv = 0.f;
-      if (k < re) {
-        if (i0 + c < d1) {
-          if (OMEGA) {
-            uint32_t s = (bits[k >> 5] >> (k & 31)) & 1u;
-            s ^= (uint32_t)(__popcll((unsigned long long)k & (unsigned long long)pc[c]) & 1);
-            lv = s ? -1.0f : 1.0f;
-          } else {
-            lv = L[k + (int64_t)(i0 + c) * ldl];
-          }
+      float lv = 0.f;
+      if (k < re && i0 + c < d1) {
+        if (OMEGA) {
+          uint32_t s = (bits[k >> 5] >> (k & 31)) & 1u;
+          s ^= (uint32_t)(__popcll((unsigned long long)k & (unsigned long long)pc[c]) & 1);
+          lv = s ? -1.0f : 1.0f;
+        } else {
+          lv = L[k + (int64_t)(i0 + c) * ldl];
         }
-        if (j0 + c < d2) mv = M[k + (int64_t)(j0 + c) * ldm];
       }
       Ls[kk][c] = lv;
-      Ms[kk][c] = mv;
+    }
+#pragma unroll
+    for (int q = 0; q < TN / 8; ++q) {
+      int e = tid + 256 * q;
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      Ms[kk][c] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, co
                                                      const float *__restrict__ A, int64_t lda,
                                                      const float *__restrict__ X, int64_t ldx, double tau, float *Rs,
                                                      int64_t ldr) {
-  __shared__ float Sh[64][17], Sl[64][17];
+  __shared__ __align__(16) float Sh[64][16], Sl[64][16];   // read as broadcast float4s
   const int tid = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * 256 + tid;
   const int c0 = blockIdx.y * 16;
@@ -196,19 +201,27 @@ __global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, co
       for (int kk = 0; kk < kmax; ++kk) {
         float q = Q[i + (int64_t)(k0 + kk) * ldq];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          float hi = Sh[kk][c];
-          float p = q * hi, e = fmaf(q, hi, -p);
-          float s, r;
-          two_sum(hs[c], p, s, r);
-          hs[c] = s;
-          lc[c] += r + fmaf(q, Sl[kk][c], e);
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float4 h4 = *reinterpret_cast<const float4 *>(&Sh[kk][4 * c4]);
+          const float4 l4 = *reinterpret_cast<const float4 *>(&Sl[kk][4 * c4]);
+          const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = 4 * c4 + u;
+            float p = q * hv[u], e = fmaf(q, hv[u], -p);
+            float sum, r;
+            two_sum(hs[c], p, sum, r);
+            hs[c] = sum;
+            lc[c] += r + fmaf(q, lv[u], e);
+          }
         }
       }
     }
   }
   if (i < n)
-    for (int c = 0; c < mc; ++c) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {       // a compile-time bound keeps hs, lc in registers
+      if (c >= mc) break;
       double qs = (double)hs[c] + (double)lc[c];
       double a = (double)A[i + (int64_t)(c0 + c) * lda];
       double x = (double)X[i + (int64_t)(c0 + c) * ldx];
@@ -492,7 +505,7 @@ __global__ void __launch_bounds__(256) k_apply_x(int64_t n, int d, int m, const 
                                                  int64_t ldq, const double *__restrict__ V,
                                                  const float *__restrict__ A, int64_t lda, float *X,
                                                  int64_t ldx, float inv_tau) {
-  __shared__ float Vs[64][33];
+  __shared__ __align__(16) float Vs[64][32];   // read as broadcast float4s
   const int tid = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * 256 + tid;
   const int c0 = blockIdx.y * 32;
@@ -512,13 +525,20 @@ __global__ void __launch_bounds__(256) k_apply_x(int64_t n, int d, int m, const 
       for (int kk = 0; kk < kmax; ++kk) {
         float q = Q[i + (int64_t)(k0 + kk) * ldq];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fmaf(q, Vs[kk][c], acc[c]);
+        for (int c4 = 0; c4 < 8; ++c4) {
+          const float4 v = *reinterpret_cast<const float4 *>(&Vs[kk][4 * c4]);
+          acc[4 * c4 + 0] = fmaf(q, v.x, acc[4 * c4 + 0]);
+          acc[4 * c4 + 1] = fmaf(q, v.y, acc[4 * c4 + 1]);
+          acc[4 * c4 + 2] = fmaf(q, v.z, acc[4 * c4 + 2]);
+          acc[4 * c4 + 3] = fmaf(q, v.w, acc[4 * c4 + 3]);
+        }
       }
     }
   }
   if (i < n)
-    for (int c = 0; c < mc; ++c)
-      X[i + (int64_t)(c0 + c) * ldx] = (A[i + (int64_t)(c0 + c) * lda] - acc[c]) * inv_tau;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)          // a compile-time bound keeps acc in registers
+      if (c < mc) X[i + (int64_t)(c0 + c) * ldx] = (A[i + (int64_t)(c0 + c) * lda] - acc[c]) * inv_tau;
 }
 
 __global__ void k_add_inplace(int64_t n, int m, float *X, int64_t ldx, const float *D, int64_t ldd) {
@@ -556,15 +576,23 @@ static Error fold_splits(int64_t count, int splits, double *part, double *G, cud
 
 Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const uint32_t *bits,
              const int32_t *cols, double oscale, const float *M, int64_t ldm, double *G, cudaStream_t st) {
-  int tx = (int)ceil_div(d1, 64), ty = (int)ceil_div(d2, 64);
+  const bool narrow = d2 <= 32;                 // 128 x 32 tiles: no lanes wasted on a thin M
+  const int TMv = narrow ? 128 : 64, TNv = narrow ? 32 : 64;
+  int tx = (int)ceil_div(d1, TMv), ty = (int)ceil_div(d2, TNv);
   int sp = splits_for(ctx, n, tx * ty);
   int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
   double *part = nullptr;
   CK_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
   dim3 grid(tx, ty, sp);
-  if (L) ::ckinv::note_launch(), k_tsprod<false><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
-  else ::ckinv::note_launch(), k_tsprod<true><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+  ::ckinv::note_launch();
+  if (narrow) {
+    if (L) k_tsprod<false, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+    else k_tsprod<true, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+  } else {
+    if (L) k_tsprod<false, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+    else k_tsprod<true, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+  }
   CK_CUDA(cudaGetLastError());
   return fold_splits((int64_t)d1 * d2, sp, part, G, st);
 }
