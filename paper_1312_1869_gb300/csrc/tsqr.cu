@@ -69,6 +69,29 @@ __device__ __forceinline__ int panel_row(bool stacked, int c0, int d, int r) {
   return stacked ? (r < NB ? c0 + r : d + r - NB) : c0 + r;
 }
 
+// Shared-memory staging of a column-major global tile, U loads in flight per thread (a
+// load-store loop would wait out one memory latency per element):
+//   dst[i * ldd + c * cstride] = c < cvalid ? src[i + c * lds] : 0,  i < rows, c < cols.
+template <typename T, int U>
+__device__ __forceinline__ void stage_tile(T *dst, int ldd, int cstride, const T *src, int64_t lds, int rows,
+                                           int cols, int cvalid) {
+  const int total = rows * cols;
+  for (int base = 0; base < total; base += (int)blockDim.x * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * (int)blockDim.x + (int)threadIdx.x;
+      const int i = e % rows, c = e / rows;
+      v[u] = (e < total && c < cvalid) ? src[i + (int64_t)c * lds] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (e < total) dst[(e % rows) * ldd + (e / rows) * cstride] = v[u];
+    }
+  }
+}
+
 template <typename T, int PT>
 __global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, int c0, int stacked) {
   extern __shared__ __align__(16) uint8_t sm_raw[];
@@ -87,9 +110,13 @@ __global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, 
   const int tid = threadIdx.x;
   T *base = M + (int64_t)c0 * H;                          // column c0
 
-  for (int c = 0; c < NB; ++c)
-    for (int r = tid; r < h; r += PT)
-      Ps[c * hp + r] = base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H];
+  if (!stacked) {
+    stage_tile<T, 8>(Ps, 1, hp, base + c0, H, h, NB, NB);
+  } else {
+    for (int c = 0; c < NB; ++c)
+      for (int r = tid; r < h; r += PT)
+        Ps[c * hp + r] = base[panel_row<T>(stacked, c0, d, r) + (int64_t)c * H];
+  }
   for (int e = tid; e < NB * NB; e += PT) Ts[e] = 0;
   __syncthreads();
 
@@ -304,8 +331,7 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = min(NBS, d - j0);
   const int rows = j0 + nb;                       // bottom rows the panel touches
-  for (int c = 0; c < nb; ++c)
-    for (int i = tid; i < rows; i += SQ_THREADS) Vp[c * d + i] = M[d + i + (int64_t)(j0 + c) * H];
+  stage_tile<T, 8>(Vp, 1, d, M + d + (int64_t)j0 * H, H, rows, nb, nb);
   for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
     const int r = e / NBS, c = e % NBS;
     Ct[e] = (r < nb && c < nb) ? M[j0 + r + (int64_t)(j0 + c) * H] : T(0);
@@ -318,8 +344,14 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
     // raw dots of x with every panel column (c == jj gives |x|^2), one warp per column
     for (int c = wid; c < nb; c += NW) {
       const T *y = Vp + c * d;
-      T acc = 0;
-      for (int i = lane; i <= j; i += 32) acc += x[i] * y[i];
+      T a0 = 0, a1 = 0;
+      int i = lane;
+      for (; i + 32 <= j; i += 64) {
+        a0 += x[i] * y[i];
+        a1 += x[i + 32] * y[i + 32];
+      }
+      if (i <= j) a0 += x[i] * y[i];
+      T acc = a0 + a1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) Dt[c] = acc;
@@ -365,6 +397,146 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
   for (int c = 0; c < nb; ++c)
     for (int i = tid; i < d; i += SQ_THREADS)
       Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] : T(0);
+}
+
+// After panel [j0, j0 + nb) of every combine, one launch does the rest of the panel's work:
+// CTAs 0 .. ceil(nt / NBS) - 1 apply the panel's block reflector to NBS trailing columns
+// each (W = C_top + V^T C_bot, W2 = T_kk^T W, C_top -= W2, C_bot -= V W2, all in shared
+// memory), and the remaining CTAs compute NBS rows each of S = V_bot[:, 0:j0]^T V_panel for
+// the panel's block of T (finished by k_sq_tblock).  V_panel and C_bot use rows 0..j0+nb-1.
+template <typename T>
+size_t sq_update_smem(int d) {
+  constexpr int NBS = sq_nb<T>();
+  return sizeof(T) * ((size_t)2 * d * (NBS + 1) + 4 * NBS * (NBS + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sq_update(T *M0, const T *Vx0, const T *Tm0, T *S0, int d, int j0) {
+  constexpr int NBS = sq_nb<T>();
+  constexpr int LD = NBS + 1;                     // padded rows of the shared tiles
+  extern __shared__ __align__(16) uint8_t sm_raw[];
+  T *Vs = reinterpret_cast<T *>(sm_raw);          // rows x NBS: the panel's V_bot
+  T *Cs = Vs + (size_t)d * LD;                    // rows x NBS: C_bot tile, or V_bot[:, l0..] for S
+  T *Ctp = Cs + (size_t)d * LD;                   // NBS x NBS: C_top tile
+  T *Tk = Ctp + NBS * LD;                         // NBS x NBS: T_kk
+  T *W = Tk + NBS * LD;                           // NBS x NBS
+  T *W2 = W + NBS * LD;
+  const int H = 2 * d;
+  const int nb = min(NBS, d - j0), rows = j0 + nb, c1 = rows, nt = d - c1;
+  const int ntile = (nt + NBS - 1) / NBS;
+  T *M = M0 + (int64_t)blockIdx.y * H * d;
+  const T *Vx = Vx0 + (int64_t)blockIdx.y * H * d;
+  const T *Tm = Tm0 + (int64_t)blockIdx.y * d * d;
+  T *S = S0 + (int64_t)blockIdx.y * d * NBS;      // j0 x nb, ld d
+  const int tid = threadIdx.x;
+  stage_tile<T, 8>(Vs, LD, 1, Vx + d + (int64_t)j0 * H, H, rows, NBS, nb);
+  if ((int)blockIdx.x < ntile) {
+    const int cb = c1 + blockIdx.x * NBS;
+    const int nc = min(NBS, d - cb);
+    stage_tile<T, 8>(Cs, LD, 1, M + d + (int64_t)cb * H, H, rows, NBS, nc);
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int r = e % NBS, cc = e / NBS;
+      Ctp[r * LD + cc] = (r < nb && cc < nc) ? M[j0 + r + (int64_t)(cb + cc) * H] : T(0);
+      Tk[r * LD + cc] = (r < nb && cc < nb) ? Tm[(j0 + r) + (int64_t)(j0 + cc) * d] : T(0);
+    }
+    __syncthreads();
+    // W = C_top + V^T C_bot
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int cc = e % NBS, r = e / NBS;
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
+      int i = 0;
+      for (; i + 4 <= rows; i += 4) {
+        a0 += Vs[i * LD + r] * Cs[i * LD + cc];
+        a1 += Vs[(i + 1) * LD + r] * Cs[(i + 1) * LD + cc];
+        a2 += Vs[(i + 2) * LD + r] * Cs[(i + 2) * LD + cc];
+        a3 += Vs[(i + 3) * LD + r] * Cs[(i + 3) * LD + cc];
+      }
+      for (; i < rows; ++i) a0 += Vs[i * LD + r] * Cs[i * LD + cc];
+      W[r * LD + cc] = Ctp[r * LD + cc] + ((a0 + a1) + (a2 + a3));
+    }
+    __syncthreads();
+    // W2 = T_kk^T W ; C_top -= W2
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int cc = e % NBS, r = e / NBS;
+      T acc = 0;
+      for (int k = 0; k <= r; ++k) acc += Tk[k * LD + r] * W[k * LD + cc];
+      W2[r * LD + cc] = acc;
+      if (r < nb && cc < nc) M[j0 + r + (int64_t)(cb + cc) * H] = Ctp[r * LD + cc] - acc;
+    }
+    __syncthreads();
+    // C_bot -= V W2
+    for (int e = tid; e < rows * NBS; e += blockDim.x) {
+      const int cc = e % NBS, i = e / NBS;
+      if (cc >= nc) continue;
+      T acc = 0;
+#pragma unroll 8
+      for (int r = 0; r < NBS; ++r) acc += Vs[i * LD + r] * W2[r * LD + cc];
+      M[d + i + (int64_t)(cb + cc) * H] = Cs[i * LD + cc] - acc;
+    }
+  } else {
+    const int l0 = (blockIdx.x - ntile) * NBS;
+    const int nl = min(NBS, j0 - l0);
+    stage_tile<T, 8>(Cs, LD, 1, Vx + d + (int64_t)l0 * H, H, rows, NBS, nl);
+    __syncthreads();
+    // S[l0 + ll][c] = V_bot[:, l0 + ll] . V_panel[:, c]  (rows 0..l0+ll carry V_bot)
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int c = e % NBS, ll = e / NBS;
+      if (ll >= nl || c >= nb) continue;
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      const int imax = min(rows, l0 + ll + 1);
+      int i = 0;
+      for (; i + 4 <= imax; i += 4) {
+        a0 += Cs[i * LD + ll] * Vs[i * LD + c];
+        a1 += Cs[(i + 1) * LD + ll] * Vs[(i + 1) * LD + c];
+        a2 += Cs[(i + 2) * LD + ll] * Vs[(i + 2) * LD + c];
+        a3 += Cs[(i + 3) * LD + ll] * Vs[(i + 3) * LD + c];
+      }
+      for (; i < imax; ++i) a0 += Cs[i * LD + ll] * Vs[i * LD + c];
+      S[(l0 + ll) + (int64_t)c * d] = (a0 + a1) + (a2 + a3);
+    }
+  }
+}
+
+// T[r][panel] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for rows r of block blockIdx.x (< j0).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sq_tblock(T *Tm0, const T *S0, int d, int j0) {
+  constexpr int NBS = sq_nb<T>();
+  constexpr int LD = NBS + 1;
+  __shared__ T Tt[NBS * LD], Sb[NBS * LD], U[NBS * LD], Tk[NBS * LD];
+  const int nb = min(NBS, d - j0);
+  T *Tm = Tm0 + (int64_t)blockIdx.y * d * d;
+  const T *S = S0 + (int64_t)blockIdx.y * d * NBS;
+  const int r0 = blockIdx.x * NBS, nr = min(NBS, j0 - r0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int a = e % NBS, b = e / NBS;
+    U[a * LD + b] = 0;
+    Tk[a * LD + b] = (a < nb && b < nb) ? Tm[(j0 + a) + (int64_t)(j0 + b) * d] : T(0);
+  }
+  for (int l0 = r0; l0 < j0; l0 += NBS) {
+    const int nl = min(NBS, j0 - l0);
+    __syncthreads();
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int a = e % NBS, b = e / NBS;         // Tt[a][b] = T[r0 + a][l0 + b];  Sb[a][b] = S[l0 + a][b]
+      Tt[a * LD + b] = (a < nr && b < nl) ? Tm[(r0 + a) + (int64_t)(l0 + b) * d] : T(0);
+      Sb[a * LD + b] = (a < nl && b < nb) ? S[(l0 + a) + (int64_t)b * d] : T(0);
+    }
+    __syncthreads();
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int c = e % NBS, a = e / NBS;
+      T acc = 0;
+      for (int l = 0; l < NBS; ++l) acc += Tt[a * LD + l] * Sb[l * LD + c];
+      U[a * LD + c] += acc;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int c = e % NBS, a = e / NBS;
+    if (a >= nr || c >= nb) continue;
+    T acc = 0;
+    for (int k = 0; k < NBS; ++k) acc += U[a * LD + k] * Tk[k * LD + c];
+    Tm[(r0 + a) + (int64_t)(j0 + c) * d] = -acc;
+  }
 }
 
 // One stage: P independent QRs of H x d matrices (strided, ld H).
@@ -505,46 +677,36 @@ Error alloc_stage(Stage<T> &s, int P, int H, int d, const std::vector<int> &top,
 //   T[0:j0, panel] = -T[0:j0, 0:j0] (V_bot[:, 0:j0]^T V_panel) T_panel,
 //   W = C_top + V_panel^T C_bot,  W2 = T_panel^T W,  C_top -= W2,  C_bot -= V_panel W2
 // on the trailing columns (rows 0..j0+nb-1 of the bottom block).
+// Panel by panel over all combines of a level: the panel kernel, then one launch for the
+// trailing update and S = V_bot[:, 0:j0]^T V_panel, then the panel's block of T:
+//   T[0:j0, panel] = -T[0:j0, 0:j0] S T_panel.
 template <typename T>
 Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st) {
   constexpr int NBS = sq_nb<T>();
-  const int H = s.H, P = s.P;
-  const int64_t sM = (int64_t)H * d, sT = (int64_t)d * d, sW = (int64_t)NBS * d;
-  const size_t smem = sq_panel_smem<T>(d);
-  CK_CUDA(cudaFuncSetAttribute(k_sq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  T *W = nullptr, *W2 = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * (size_t)P * sW, st));
-  CK_CUDA(cudaMallocAsync((void **)&W2, sizeof(T) * (size_t)P * sW, st));
+  const int P = s.P;
+  const size_t psmem = sq_panel_smem<T>(d), usmem = sq_update_smem<T>(d);
+  CK_CUDA(cudaFuncSetAttribute(k_sq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  CK_CUDA(cudaFuncSetAttribute(k_sq_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
+  T *S = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&S, sizeof(T) * (size_t)P * d * NBS, st));
   Error e = ok();
   for (int j0 = 0; j0 < d && !e.st; j0 += NBS) {
-    const int nb = std::min(NBS, d - j0), rows = j0 + nb, nt = d - rows;
+    const int nb = std::min(NBS, d - j0), nt = d - j0 - nb;
+    const int ntile = (nt + NBS - 1) / NBS, nstile = (j0 + NBS - 1) / NBS;
     note_launch();
-    k_sq_panel<T><<<P, SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, d, j0);
+    k_sq_panel<T><<<P, SQ_THREADS, psmem, st>>>(s.M, s.Vx, s.Tm, d, j0);
+    if (ntile + nstile > 0) {
+      note_launch();
+      k_sq_update<T><<<dim3((unsigned)(ntile + nstile), (unsigned)P), 256, usmem, st>>>(s.M, s.Vx, s.Tm, S, d, j0);
+    }
+    if (nstile > 0) {
+      note_launch();
+      k_sq_tblock<T><<<dim3((unsigned)nstile, (unsigned)P), 256, 0, st>>>(s.Tm, S, d, j0);
+    }
     cudaError_t ce = cudaGetLastError();
-    if (ce != cudaSuccess) { e = fail(CKINV_ECUDA, cudaGetErrorString(ce)); break; }
-    T *Vb = s.Vx + d;                          // V_bot, ld H
-    T *Vpan = Vb + (int64_t)j0 * H;
-    T *Tkk = s.Tm + j0 + (int64_t)j0 * d;
-    if (j0 > 0) {
-      // S (j0 x nb, ld j0) = V_bot[0:rows, 0:j0]^T V_panel ; U = T11 S ; T12 = -U T_kk
-      if ((e = gemm_batched<T>(ctx, true, j0, nb, rows, T(1), Vb, H, sM, Vpan, H, sM, T(0), W, j0, sW, P, st)).st) break;
-      if ((e = gemm_batched<T>(ctx, false, j0, nb, j0, T(1), s.Tm, d, sT, W, j0, sW, T(0), W2, j0, sW, P, st)).st) break;
-      if ((e = gemm_batched<T>(ctx, false, j0, nb, nb, T(-1), W2, j0, sW, Tkk, d, sT, T(0), s.Tm + (int64_t)j0 * d, d,
-                               sT, P, st)).st)
-        break;
-    }
-    if (nt > 0) {
-      T *Ct = s.M + j0 + (int64_t)rows * H;    // top rows of the panel, trailing columns
-      T *Cb = s.M + d + (int64_t)rows * H;     // bottom rows 0..rows-1, trailing columns
-      if ((e = axpby<T>(nb, nt, T(1), Ct, H, sM, T(0), W, nb, sW, P, st)).st) break;
-      if ((e = gemm_batched<T>(ctx, true, nb, nt, rows, T(1), Vpan, H, sM, Cb, H, sM, T(1), W, nb, sW, P, st)).st) break;
-      if ((e = gemm_batched<T>(ctx, true, nb, nt, nb, T(1), Tkk, d, sT, W, nb, sW, T(0), W2, nb, sW, P, st)).st) break;
-      if ((e = axpby<T>(nb, nt, T(-1), W2, nb, sW, T(1), Ct, H, sM, P, st)).st) break;
-      if ((e = gemm_batched<T>(ctx, false, rows, nt, nb, T(-1), Vpan, H, sM, W2, nb, sW, T(1), Cb, H, sM, P, st)).st) break;
-    }
+    if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
   }
-  cudaFreeAsync(W, st);
-  cudaFreeAsync(W2, st);
+  cudaFreeAsync(S, st);
   return e;
 }
 
