@@ -92,6 +92,13 @@ Error check_plan(const ckinv_plan_desc *plan, const ckinv_kernel *kern, bool nee
   return ok();
 }
 
+// The BF16 forms run the TSQR's large FP32 GEMMs on the tensor cores (three BF16 terms
+// per operand, FP32 accumulation in TMEM: R and Q_hat to ~1e-5, below those forms' sketch
+// error); the FP32 form and FP64 leaves keep them on the CUDA cores (~1e-7).
+bool tsqr_on_tensor_cores(const ckinv_plan_desc *plan) {
+  return plan->prec != CKINV_FP32 && plan->leaf_fp64 == 0;
+}
+
 KernelParams make_params(const ckinv_plan_desc *plan, const ckinv_kernel *kern) {
   KernelParams kp;
   kp.kind = kern->kind;
@@ -153,12 +160,13 @@ void factor_release(ckinv_factor *f) {
 }
 
 // ------------------------------------------------------------------ leaf-height autotuner
-// Chosen TSQR leaf heights, keyed by (device, d, ceil(log2 n), FP64 tree levels, FP64 leaves).
+// Chosen TSQR leaf heights, keyed by (device, d, ceil(log2 n), FP64 tree levels, FP64 leaves,
+// tensor-core GEMMs).
 struct TuneKey {
-  int device, d, log2n, fp64_levels, leaf_fp64;
+  int device, d, log2n, fp64_levels, leaf_fp64, tc;
   bool operator<(const TuneKey &o) const {
-    return std::tie(device, d, log2n, fp64_levels, leaf_fp64) <
-           std::tie(o.device, o.d, o.log2n, o.fp64_levels, o.leaf_fp64);
+    return std::tie(device, d, log2n, fp64_levels, leaf_fp64, tc) <
+           std::tie(o.device, o.d, o.log2n, o.fp64_levels, o.leaf_fp64, o.tc);
   }
 };
 std::mutex g_tune_mu;
@@ -167,7 +175,7 @@ std::map<TuneKey, int> g_tuned;
 TuneKey tune_key(const ckinv_ctx *ctx, const ckinv_plan_desc *plan) {
   int l = 0;
   while (((int64_t)1 << l) < plan->n) ++l;
-  return TuneKey{ctx->device, plan->d, l, plan->tree_fp64_levels, plan->leaf_fp64};
+  return TuneKey{ctx->device, plan->d, l, plan->tree_fp64_levels, plan->leaf_fp64, tsqr_on_tensor_cores(plan) ? 1 : 0};
 }
 
 int leaf_rows(const ckinv_ctx *ctx, const ckinv_plan_desc *plan) {
@@ -217,10 +225,10 @@ Error autotune_leaf_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan, cudaStream
     note_launch();
     k_fill_hash<<<(unsigned)std::min<int64_t>(ceil_div(n * d, 256), 4096), 256, 0, st>>>(n * d, 0x9e3779b9u, Y);
     for (int b : cand) {
-      if ((e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, Y, n, Q, R, st)).st) break;
+      if ((e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, tsqr_on_tensor_cores(plan), Y, n, Q, R, st)).st) break;
       cudaEventRecord(e0, st);
       for (int r = 0; r < 2 && !e.st; ++r)
-        e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, Y, n, Q, R, st);
+        e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, tsqr_on_tensor_cores(plan), Y, n, Q, R, st);
       cudaEventRecord(e1, st);
       if (e.st) break;
       if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -294,7 +302,8 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
     if (c1 != cudaSuccess || c2 != cudaSuccess) e = fail(CKINV_ECUDA, "copy of Omega into the factor failed");
   }
   if (e.st == CKINV_OK) {
-    e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, Y, ldy, f->Q, f->R, st);
+    e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, tsqr_on_tensor_cores(plan), Y, ldy, f->Q,
+                    f->R, st);
   }
   if (e.st == CKINV_OK) e = lowrank_core(ctx, f, st);
   if (e.st != CKINV_OK) {

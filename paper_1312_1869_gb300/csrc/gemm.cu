@@ -175,6 +175,11 @@ Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alp
     if (beta == T(1)) return ok();
     return fail(CKINV_EINVAL, "gemm_batched: K = 0 with beta != 1");
   }
+  // FP32 products big enough to fill 128 x 128 tensor-core tiles go to the tensor cores
+  if (sizeof(T) == 4 && ctx->gemm_tc && M >= 64 && N >= 64 && K >= 64 &&
+      (double)M * N * (double)K * batch >= 3.0e7)
+    return gemm_tc_f32(ctx, transA, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
+                       (float)beta, (float *)C, ldc, sC, batch, st);
   // tile choice: 128 x 128 (8 x 8 per thread) for large FP32 outputs, else 64 x 64 (4 x 4)
   const bool big = (sizeof(T) == 4) && M >= 256 && N >= 128;
   const int bm = big ? 128 : 64, bn = big ? 128 : 64;

@@ -97,6 +97,9 @@ struct ckinv_ctx {
   size_t cand_cap = 0;
   // set while the context's work is being captured into a CUDA graph
   ckinv::UploadArena *capture_arena = nullptr;
+  // FP32 GEMMs on the tensor cores (split BF16) rather than the CUDA cores; set by
+  // tsqr_factor for the duration of one factorization
+  bool gemm_tc = false;
 };
 
 struct ckinv_factor {
@@ -172,12 +175,16 @@ struct TsqrOut {
   float *Q;     // n x d (ld n), explicit, column signs folded in
   double *R;    // d x d, diag >= 0
 };
-Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64,
+Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
                   const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
 int auto_block_rows(int64_t n, int d, int sm_count);
 
 // ----------------------------------------------------------------------------- GEMM
 // C_b = alpha op(A_b) B_b + beta C_b for b < batch (column-major, strided batches).
+// FP32 batched GEMM on the tensor cores (three BF16 terms per operand, six products).
+Error gemm_tc_f32(const ckinv_ctx *ctx, bool transA, int M, int N, int K, float alpha, const float *A, int64_t lda,
+                  int64_t sA, const float *B, int64_t ldb, int64_t sB, float beta, float *C, int64_t ldc, int64_t sC,
+                  int batch, cudaStream_t st);
 template <typename T>
 Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
                    int64_t sA, const T *B, int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC,

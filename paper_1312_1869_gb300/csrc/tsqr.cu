@@ -892,8 +892,15 @@ int auto_block_rows(int64_t n, int d, int sm_count) {
   return (int)b;
 }
 
-Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, const float *Y,
-                  int64_t ldy, float *Qout, double *Rout, cudaStream_t st) {
+Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
+                  const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st) {
+  // the FP32 GEMMs of this factorization on the tensor cores or on the CUDA cores
+  struct Restore {
+    ckinv_ctx *c;
+    bool v;
+    ~Restore() { c->gemm_tc = v; }
+  } restore{ctx, ctx->gemm_tc};
+  ctx->gemm_tc = tc_gemm;
   if (d % NB != 0) return fail(CKINV_EINVAL, "tsqr: d must be a multiple of 16");
   const int bmax = max_block_rows(d, leaf_fp64);
   if (bmax < d) return fail(CKINV_EUNSUPPORTED, "tsqr: d too large for a shared-memory panel");

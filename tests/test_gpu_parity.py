@@ -144,6 +144,31 @@ def test_tsqr_matches_oracle(ctx, n, d, b, f64, leaf64):
     assert np.abs(Q.T @ Q - np.eye(d)).max() <= (1e-6 if leaf64 else 1e-5)
 
 
+@pytest.mark.parametrize("n,d,b", [(20000, 128, 1024), (9000, 512, 2048)])
+def test_tsqr_bf16_forms_tensor_core_gemms(ctx, n, d, b):
+    """A BF16-form plan runs the TSQR's large GEMMs on the tensor cores (each FP32 operand as
+    three BF16 terms, FP32 accumulation in TMEM).  The accumulation is coarser than FP32
+    FMAs: measured R 6.3e-6, Q_hat 1.9e-5 and |Q^T Q - I| 1.0e-5 at n = 9000, d = 512, against
+    9e-8, 5e-7 and 5e-7 on the CUDA cores (nine term products instead of six change nothing,
+    so the dropped products are not the cause).  The bars below leave ~3x margin; they sit
+    far under those forms' sketch error (BF16: ~1.5e-3)."""
+    rng = np.random.default_rng(n + d)
+    Y = rng.standard_normal((n, d)).astype(np.float32)
+    plan = ck.Plan(n=n, d=d, block_rows=b, seed=1, prec=ck.BF16, tree_fp64_levels=1)
+    f = ck.tsqr(ctx, plan, ck.Kernel(ck.SE, 1, 1, 1e-3), col(Y))
+    R = host(f.r())
+    Q = host(f.q())
+    torch.cuda.synchronize()
+    ck.check(ctx)
+    t = ots.tsqr(Y.astype(np.float64), b)
+    orth = np.abs(Q.T.astype(np.float64) @ Q - np.eye(d)).max()
+    print("tsqr (tensor-core GEMMs) n=%d d=%d: R %.3e Q %.3e orth %.3e" % (n, d, rel(R, t["R"]), rel(Q, t["Q"]), orth))
+    assert np.allclose(R, np.triu(R)) and np.all(np.diag(R) >= 0)
+    assert rel(R, t["R"]) <= 2e-5
+    assert rel(Q, t["Q"]) <= 6e-5
+    assert orth <= 3e-5
+
+
 def test_core_matches_oracle(ctx):
     n, d, b, tau = 4096, 64, 1024, 1e-3
     rng = np.random.default_rng(5)
