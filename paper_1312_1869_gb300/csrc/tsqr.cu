@@ -305,12 +305,12 @@ Error axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta
 // compact-WY factor T are batched GEMMs over all combines of the level (sq_factor).
 template <typename T>
 constexpr int sq_nb() { return sizeof(T) == 4 ? 32 : 16; }
-constexpr int SQ_THREADS = 256;
+constexpr int SQ_THREADS = 512;
 
 template <typename T>
 size_t sq_panel_smem(int d) {
   constexpr int NBS = sq_nb<T>();
-  return sizeof(T) * ((size_t)d * NBS + 2 * NBS * NBS + NBS + 4);
+  return sizeof(T) * ((size_t)d * NBS + 2 * NBS * NBS + 2 * NBS + 4);
 }
 
 // Panel [j0, j0 + nb) of every combine: R rows into the top of S, V_bot columns into rows
@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
   T *Ct = Vp + (size_t)NBS * d;                   // NBS x NBS top block, row-major
   T *Tk = Ct + NBS * NBS;                         // NBS x NBS panel T, row-major
   T *Dt = Tk + NBS * NBS;                         // NBS raw dots of the current step
+  T *Ih = Dt + NBS;                               // 1 / head of each reflector (Vp keeps x unscaled)
   const int H = 2 * d;
   T *M = M0 + (int64_t)blockIdx.x * H * d;
   T *Vx = Vx0 + (int64_t)blockIdx.x * H * d;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
     const int j = j0 + jj;                        // bottom rows 0..j are active
-    const T *x = Vp + jj * d;
+    const T *x = Vp + jj * d;                     // unscaled: the reflector is x / head
     // raw dots of x with every panel column (c == jj gives |x|^2), one warp per column
     for (int c = wid; c < nb; c += NW) {
       const T *y = Vp + c * d;
@@ -371,21 +372,24 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
     // the rest of the panel: w_c = Ct[jj][c] + (x . col_c) / head, then the reflection
     for (int c = jj + 1 + wid; c < nb; c += NW) {
       const T w = tau * (Ct[jj * NBS + c] + Dt[c] * inv_head);
+      const T g = w * inv_head;
       T *col = Vp + c * d;
-      for (int i = lane; i <= j; i += 32) col[i] -= w * x[i] * inv_head;
+      for (int i = lane; i <= j; i += 32) col[i] -= g * x[i];
       if (lane == 0) Ct[jj * NBS + c] -= w;
     }
-    // T within the panel: T[r][jj] = -tau sum_{l=r}^{jj-1} T[r][l] (v_l . v_jj)
-    if (tid < jj) {
-      T acc = 0;
-      for (int l = tid; l < jj; ++l) acc += Tk[tid * NBS + l] * (Dt[l] * inv_head);
-      Tk[tid * NBS + jj] = -tau * acc;
+    // T within the panel: T[r][jj] = -tau sum_{l=r}^{jj-1} T[r][l] (v_l . v_jj), one warp
+    // per row r, with v_l . v_jj = Dt[l] Ih[l] inv_head
+    for (int r = wid; r < jj; r += NW) {
+      T t = 0;
+      for (int l = r + lane; l < jj; l += 32) t += Tk[r * NBS + l] * (Dt[l] * Ih[l]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) Tk[r * NBS + jj] = -tau * inv_head * t;
     }
-    __syncthreads();
-    for (int i = tid; i <= j; i += SQ_THREADS) Vp[jj * d + i] = x[i] * inv_head;
     if (tid == 0) {
       Ct[jj * NBS + jj] = rd;
       Tk[jj * NBS + jj] = tau;
+      Ih[jj] = inv_head;
     }
     __syncthreads();
   }
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
   }
   for (int c = 0; c < nb; ++c)
     for (int i = tid; i < d; i += SQ_THREADS)
-      Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] : T(0);
+      Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] * Ih[c] : T(0);
 }
 
 // After panel [j0, j0 + nb) of every combine, one launch does the rest of the panel's work:
@@ -411,7 +415,7 @@ size_t sq_update_smem(int d) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sq_update(T *M0, const T *Vx0, const T *Tm0, T *S0, int d, int j0) {
+__global__ void __launch_bounds__(SQ_THREADS) k_sq_update(T *M0, const T *Vx0, const T *Tm0, T *S0, int d, int j0) {
   constexpr int NBS = sq_nb<T>();
   constexpr int LD = NBS + 1;                     // padded rows of the shared tiles
   extern __shared__ __align__(16) uint8_t sm_raw[];
@@ -499,7 +503,7 @@ __global__ void __launch_bounds__(256) k_sq_update(T *M0, const T *Vx0, const T 
 
 // T[r][panel] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for rows r of block blockIdx.x (< j0).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sq_tblock(T *Tm0, const T *S0, int d, int j0) {
+__global__ void __launch_bounds__(SQ_THREADS) k_sq_tblock(T *Tm0, const T *S0, int d, int j0) {
   constexpr int NBS = sq_nb<T>();
   constexpr int LD = NBS + 1;
   __shared__ T Tt[NBS * LD], Sb[NBS * LD], U[NBS * LD], Tk[NBS * LD];
@@ -697,11 +701,11 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st)
     k_sq_panel<T><<<P, SQ_THREADS, psmem, st>>>(s.M, s.Vx, s.Tm, d, j0);
     if (ntile + nstile > 0) {
       note_launch();
-      k_sq_update<T><<<dim3((unsigned)(ntile + nstile), (unsigned)P), 256, usmem, st>>>(s.M, s.Vx, s.Tm, S, d, j0);
+      k_sq_update<T><<<dim3((unsigned)(ntile + nstile), (unsigned)P), SQ_THREADS, usmem, st>>>(s.M, s.Vx, s.Tm, S, d, j0);
     }
     if (nstile > 0) {
       note_launch();
-      k_sq_tblock<T><<<dim3((unsigned)nstile, (unsigned)P), 256, 0, st>>>(s.Tm, S, d, j0);
+      k_sq_tblock<T><<<dim3((unsigned)nstile, (unsigned)P), SQ_THREADS, 0, st>>>(s.Tm, S, d, j0);
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
