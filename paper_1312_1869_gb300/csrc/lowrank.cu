@@ -333,13 +333,15 @@ __global__ void k_lu_trsm(int d, int k0, int kb, double *A0) {
 // ---------------------------------------------------------------- triangular solves
 // X (d x m, ld d) <- op(A)^-1 X with A = P L U packed (LAPACK interchanges), d <= 512.
 // One warp per right-hand side, its vector in registers (element i in lane i % 32, slot
-// i / 32), kSolveWarps right-hand sides per block sharing the factor: the columns of L
-// and U are staged through shared memory kSolveChunk at a time by the whole block, so a
-// step costs a shared-memory read and a shuffle, not an L2 round trip.  L and U are
-// applied by columns; U^T and L^T in dot-product form (a column per step, then a warp
-// sum).  The interchanges go through a per-warp shared-memory copy of the vector.
+// i / 32), kSolveWarps right-hand sides per block sharing the factor.  The columns of L
+// and U stream through two shared-memory buffers of kSolveChunk columns: the block
+// copies the next chunk asynchronously (cp.async, no registers held) while it works on
+// the current one, so a step costs a shared-memory read and a shuffle, not an L2 round
+// trip.  L and U are applied by columns; U^T and L^T in dot-product form (a column per
+// step, then a warp sum).  The interchanges go through a per-warp shared-memory copy of
+// the vector.
 constexpr int kSolveSlots = 16;
-constexpr int kSolveWarps = 8;
+constexpr int kSolveWarps = 1;   // one right-hand side per block: the FP64 FMAs spread over SMs
 constexpr int kSolveChunk = 16;
 __device__ __forceinline__ double slot_get(const double (&v)[kSolveSlots], int s) {
   double r = 0.0;
@@ -356,26 +358,49 @@ __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(double *dst, const double *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __global__ void __launch_bounds__(32 * kSolveWarps) k_lu_solve(int d, int m, const double *__restrict__ LU,
                                                                const int32_t *__restrict__ piv, double *X,
                                                                int trans) {
-  extern __shared__ double sm[];
-  double *cols = sm;                                   // kSolveChunk columns, ld d
-  double *xs = sm + (size_t)kSolveChunk * d + (size_t)(threadIdx.x >> 5) * d;
+  extern __shared__ __align__(16) double sm[];
+  double *cols = sm;                                   // two buffers of kSolveChunk columns, ld d
+  double *xs = sm + (size_t)2 * kSolveChunk * d + (size_t)(threadIdx.x >> 5) * d;
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * kSolveWarps + (threadIdx.x >> 5);
-  const bool active = c < m;                           // idle warps still stage columns
+  const bool active = c < m;                           // idle warps still copy columns
   double *x = X + (int64_t)(active ? c : 0) * d;
   double v[kSolveSlots];
   const int nchunk = (d + kSolveChunk - 1) / kSolveChunk;
-  // stage columns [j0, j0 + kSolveChunk) of LU
-  auto stage = [&](int ch) {
-    __syncthreads();
+  // chunk-steps 0 .. 2 nchunk - 1: first pass ascending, second pass descending
+  auto chunk_of = [&](int k) { return k < nchunk ? k : 2 * nchunk - 1 - k; };
+  const bool wide = ((d & 1) == 0) && ((reinterpret_cast<uintptr_t>(LU) & 15) == 0);
+  // copy columns [j0, j0 + kSolveChunk) of LU (contiguous) into buffer b
+  auto issue = [&](int ch, int b) {
     const int j0 = ch * kSolveChunk;
-    const int w = min(kSolveChunk, d - j0);
-    for (int e = threadIdx.x; e < w * d; e += blockDim.x) cols[e] = LU[(int64_t)j0 * d + e];
-    __syncthreads();
+    const int total = min(kSolveChunk, d - j0) * d;
+    const double *src = LU + (int64_t)j0 * d;
+    double *dst = cols + (size_t)b * kSolveChunk * d;
+    if (wide) {
+      for (int e = 2 * (int)threadIdx.x; e < total; e += 2 * (int)blockDim.x) cp_async16(dst + e, src + e);
+    } else {
+      for (int e = threadIdx.x; e < total; e += blockDim.x) cp_async8(dst + e, src + e);
+    }
+    cp_async_commit();
   };
   auto swaps = [&](bool forward) {
     if (lane == 0 && active) {
@@ -393,78 +418,92 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_lu_solve(int d, int m, con
     }
     __syncwarp();
   };
+  issue(0, 0);
   if (!trans) {
     if (active) for (int i = lane; i < d; i += 32) xs[i] = x[i];
     __syncwarp();
     swaps(true);
 #pragma unroll
     for (int s = 0; s < kSolveSlots; ++s) v[s] = (s * 32 + lane < d) ? xs[s * 32 + lane] : 0.0;
-    for (int ch = 0; ch < nchunk; ++ch) {            // L y = P x  (unit lower), by columns
-      stage(ch);
-      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
-      for (int j = j0; j < j1; ++j) {
-        const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31);
-        const double *col = cols + (size_t)(j - j0) * d;
+  } else {
 #pragma unroll
-        for (int s = 0; s < kSolveSlots; ++s) {
-          const int i = s * 32 + lane;
-          if (i > j && i < d) v[s] = fma(-col[i], xj, v[s]);
+    for (int s = 0; s < kSolveSlots; ++s) v[s] = (active && s * 32 + lane < d) ? x[s * 32 + lane] : 0.0;
+  }
+  for (int k = 0; k < 2 * nchunk; ++k) {
+    if (k + 1 < 2 * nchunk) {
+      issue(chunk_of(k + 1), (k + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const double *cb = cols + (size_t)(k & 1) * kSolveChunk * d;
+    const int ch = chunk_of(k);
+    const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
+    if (!trans) {
+      if (k < nchunk) {
+        for (int j = j0; j < j1; ++j) {                // L y = P x  (unit lower), by columns
+          const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31);
+          const double *col = cb + (size_t)(j - j0) * d;
+#pragma unroll
+          for (int s = 0; s < kSolveSlots; ++s) {
+            if (s * 32 + 31 <= j || s * 32 >= d) continue;   // no active row in this slot
+            const int i = s * 32 + lane;
+            if (i > j && i < d) v[s] = fma(-col[i], xj, v[s]);
+          }
+        }
+      } else {
+        for (int j = j1 - 1; j >= j0; --j) {           // U x = y, by columns
+          const double *col = cb + (size_t)(j - j0) * d;
+          const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31) / col[j];
+          if (lane == (j & 31)) slot_set(v, j >> 5, xj);
+#pragma unroll
+          for (int s = 0; s < kSolveSlots; ++s) {
+            if (s * 32 >= j) continue;
+            const int i = s * 32 + lane;
+            if (i < j) v[s] = fma(-col[i], xj, v[s]);
+          }
+        }
+      }
+    } else {
+      // A^T = U^T L^T P:  U^T z = x (lower), L^T w = z (unit upper), x = P^T w
+      if (k < nchunk) {
+        for (int j = j0; j < j1; ++j) {                // z_j = (x_j - sum_{i<j} U_ij z_i) / U_jj
+          const double *col = cb + (size_t)(j - j0) * d;
+          double part = 0.0;
+#pragma unroll
+          for (int s = 0; s < kSolveSlots; ++s) {
+            if (s * 32 >= j) continue;
+            const int i = s * 32 + lane;
+            if (i < j) part = fma(col[i], v[s], part);
+          }
+          const double tot = warp_sum(part);
+          if (lane == (j & 31)) slot_set(v, j >> 5, (slot_get(v, j >> 5) - tot) / col[j]);
+        }
+      } else {
+        for (int j = j1 - 1; j >= j0; --j) {           // w_j = z_j - sum_{i>j} L_ij w_i
+          const double *col = cb + (size_t)(j - j0) * d;
+          double part = 0.0;
+#pragma unroll
+          for (int s = 0; s < kSolveSlots; ++s) {
+            if (s * 32 + 31 <= j || s * 32 >= d) continue;
+            const int i = s * 32 + lane;
+            if (i > j && i < d) part = fma(col[i], v[s], part);
+          }
+          const double tot = warp_sum(part);
+          if (lane == (j & 31)) slot_set(v, j >> 5, slot_get(v, j >> 5) - tot);
         }
       }
     }
-    for (int ch = nchunk - 1; ch >= 0; --ch) {       // U x = y, by columns
-      stage(ch);
-      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
-      for (int j = j1 - 1; j >= j0; --j) {
-        const double *col = cols + (size_t)(j - j0) * d;
-        const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31) / col[j];
-        if (lane == (j & 31)) slot_set(v, j >> 5, xj);
-#pragma unroll
-        for (int s = 0; s < kSolveSlots; ++s) {
-          const int i = s * 32 + lane;
-          if (i < j) v[s] = fma(-col[i], xj, v[s]);
-        }
-      }
-    }
+    __syncthreads();                                   // buffer k & 1 is refilled at step k + 2
+  }
+  if (!trans) {
     if (active) {
 #pragma unroll
       for (int s = 0; s < kSolveSlots; ++s)
         if (s * 32 + lane < d) x[s * 32 + lane] = v[s];
     }
   } else {
-    // A^T = U^T L^T P:  U^T z = x (lower), L^T w = z (unit upper), x = P^T w
-#pragma unroll
-    for (int s = 0; s < kSolveSlots; ++s) v[s] = (active && s * 32 + lane < d) ? x[s * 32 + lane] : 0.0;
-    for (int ch = 0; ch < nchunk; ++ch) {            // z_j = (x_j - sum_{i<j} U_ij z_i) / U_jj
-      stage(ch);
-      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
-      for (int j = j0; j < j1; ++j) {
-        const double *col = cols + (size_t)(j - j0) * d;
-        double part = 0.0;
-#pragma unroll
-        for (int s = 0; s < kSolveSlots; ++s) {
-          const int i = s * 32 + lane;
-          if (i < j) part = fma(col[i], v[s], part);
-        }
-        const double tot = warp_sum(part);
-        if (lane == (j & 31)) slot_set(v, j >> 5, (slot_get(v, j >> 5) - tot) / col[j]);
-      }
-    }
-    for (int ch = nchunk - 1; ch >= 0; --ch) {       // w_j = z_j - sum_{i>j} L_ij w_i
-      stage(ch);
-      const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
-      for (int j = j1 - 1; j >= j0; --j) {
-        const double *col = cols + (size_t)(j - j0) * d;
-        double part = 0.0;
-#pragma unroll
-        for (int s = 0; s < kSolveSlots; ++s) {
-          const int i = s * 32 + lane;
-          if (i > j && i < d) part = fma(col[i], v[s], part);
-        }
-        const double tot = warp_sum(part);
-        if (lane == (j & 31)) slot_set(v, j >> 5, slot_get(v, j >> 5) - tot);
-      }
-    }
 #pragma unroll
     for (int s = 0; s < kSolveSlots; ++s)
       if (s * 32 + lane < d) xs[s * 32 + lane] = v[s];
@@ -644,9 +683,9 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
 
 static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
   if (d > 32 * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
-  const size_t smem = sizeof(double) * (size_t)(kSolveChunk + kSolveWarps) * d;
+  const size_t smem = sizeof(double) * (size_t)(2 * kSolveChunk + kSolveWarps) * d;
   CK_CUDA(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(double) * (kSolveChunk + kSolveWarps) * 512)));
+                               (int)(sizeof(double) * (2 * kSolveChunk + kSolveWarps) * 512)));
   ::ckinv::note_launch(), k_lu_solve<<<(unsigned)ceil_div(m, kSolveWarps), 32 * kSolveWarps, smem, st>>>(d, m, LU, piv,
                                                                                                        X, trans);
   CK_CUDA(cudaGetLastError());
