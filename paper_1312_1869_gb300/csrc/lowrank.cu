@@ -235,72 +235,98 @@ __global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, co
 // loaded into shared memory and factored there (pivot search, interchange within the
 // panel, scaling, rank-1 updates); piv[j] is the LAPACK interchange and logabs[m]
 // accumulates log|U_jj|.  The interchanges are applied to the other columns afterwards
-// (k_lu_laswp).
+// (k_lu_laswp).  FP64 instructions are scarce on this part (an FP64 warp instruction
+// holds a scheduler's FP64 unit for 64 cycles), so the pivot search compares |x| as
+// integer keys (the bits of a non-negative double order like its value), one thread forms
+// the pivot's reciprocal, and the logarithms of the panel's diagonal are taken together at
+// the end.  Per column: one barrier after the warps post their candidates (every thread
+// then picks the winner itself), one after the interchange, one after the update.
 constexpr int kLuPanelThreads = 512;
 __global__ void __launch_bounds__(kLuPanelThreads) k_lu_panel(int d, int k0, int kb, double *A0, int32_t *piv0,
                                                               double *logabs, int *err) {
   extern __shared__ double P[];          // (d - k0) x kb, ld R
-  __shared__ double wval[kLuPanelThreads / 32];
+  __shared__ unsigned long long wkey[kLuPanelThreads / 32];
+  __shared__ double wsgn[kLuPanelThreads / 32];
   __shared__ int widx[kLuPanelThreads / 32];
-  __shared__ int s_p;
+  __shared__ double s_inv;
   const int m = blockIdx.x;
   double *A = A0 + (int64_t)m * d * d;
   int32_t *piv = piv0 + (int64_t)m * d;
   const int R = d - k0;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int c = 0; c < kb; ++c)
-    for (int i = tid; i < R; i += blockDim.x) P[i + c * R] = A[(k0 + i) + (int64_t)(k0 + c) * d];
+  const int nw = (int)(blockDim.x >> 5);
+  for (int c0 = 0; c0 < kb; c0 += 8) {   // eight loads in flight per thread
+    for (int i = tid; i < R; i += blockDim.x) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = (c0 + u < kb) ? A[(k0 + i) + (int64_t)(k0 + c0 + u) * d] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < kb) P[i + (c0 + u) * R] = t[u];
+    }
+  }
   __syncthreads();
-  double la = 0.0;
   for (int j = 0; j < kb; ++j) {
     // pivot: largest |P[i, j]| over i >= j, ties to the smaller row
-    double best = -1.0;
+    unsigned long long best = 0ull;
+    double bsg = 0.0;
     int bi = j;
     for (int i = j + tid; i < R; i += blockDim.x) {
-      double v = fabs(P[i + j * R]);
-      if (v > best) { best = v; bi = i; }
+      const double x = P[i + j * R];
+      const unsigned long long k = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+      if (k > best) { best = k; bsg = x; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      const unsigned long long ok = __shfl_down_sync(0xffffffffu, best, o);
+      const double os = __shfl_down_sync(0xffffffffu, bsg, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ok > best || (ok == best && oi < bi)) { best = ok; bsg = os; bi = oi; }
     }
-    if (lane == 0) { wval[wid] = best; widx[wid] = bi; }
+    if (lane == 0) { wkey[wid] = best; wsgn[wid] = bsg; widx[wid] = bi; }
     __syncthreads();
-    if (tid == 0) {
-      double bv = wval[0];
-      int bj = widx[0];
-      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
-        if (wval[w] > bv || (wval[w] == bv && widx[w] < bj)) { bv = wval[w]; bj = widx[w]; }
-      s_p = bj;
+    unsigned long long bk = wkey[0];
+    int p = widx[0], pw = 0;
+    for (int w = 1; w < nw; ++w) {
+      const unsigned long long k = wkey[w];
+      const int xi = widx[w];
+      if (k > bk || (k == bk && xi < p)) { bk = k; p = xi; pw = w; }
     }
-    __syncthreads();
-    const int p = s_p;
     if (p != j && tid < kb) {
-      double t = P[j + tid * R];
+      const double t = P[j + tid * R];
       P[j + tid * R] = P[p + tid * R];
       P[p + tid * R] = t;
     }
-    __syncthreads();
-    const double pv = P[j + j * R];
     if (tid == 0) {
       piv[k0 + j] = k0 + p;
-      if (pv == 0.0) atomicOr(err, DERR_SINGULAR);
-      else la += log(fabs(pv));
+      if (bk == 0ull) {
+        atomicOr(err, DERR_SINGULAR);
+        s_inv = 0.0;
+      } else {
+        s_inv = 1.0 / wsgn[pw];
+      }
     }
-    const double inv = (pv != 0.0) ? 1.0 / pv : 0.0;
-    for (int i = j + 1 + tid; i < R; i += blockDim.x) P[i + j * R] *= inv;
     __syncthreads();
-    for (int i = j + 1 + tid; i < R; i += blockDim.x) {   // rank-1 update of the rest of the panel
-      const double l = P[i + j * R];
+    const double inv = s_inv;
+    for (int i = j + 1 + tid; i < R; i += blockDim.x) {   // scale, then rank-1 update of the row
+      const double l = P[i + j * R] * inv;
+      P[i + j * R] = l;
       for (int c = j + 1; c < kb; ++c) P[i + c * R] = fma(-l, P[j + c * R], P[i + c * R]);
     }
     __syncthreads();
   }
   for (int c = 0; c < kb; ++c)
     for (int i = tid; i < R; i += blockDim.x) A[(k0 + i) + (int64_t)(k0 + c) * d] = P[i + c * R];
-  if (tid == 0) logabs[m] += la;
+  if (wid == 0) {                        // sum of log|U_jj| over the panel, fixed order
+    double la = 0.0;
+    for (int j = lane; j < kb; j += 32) {
+      const double u = P[j + j * R];
+      if (u != 0.0) la += log(fabs(u));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) la += __shfl_xor_sync(0xffffffffu, la, o);
+    if (lane == 0) logabs[m] += la;
+  }
 }
 
 // The panel's interchanges (rows k0 .. k0+kb-1) applied to every column outside the panel.
@@ -317,32 +343,50 @@ __global__ void k_lu_laswp(int d, int k0, int kb, double *A0, const int32_t *piv
   }
 }
 
-// A[k0:k0+kb, k0+kb:d] <- L11^-1 A[k0:k0+kb, k0+kb:d]  (L11 unit lower), one thread per column.
-__global__ void k_lu_trsm(int d, int k0, int kb, double *A0) {
+// A[k0:k0+kb, k0+kb:d] <- L11^-1 A[k0:k0+kb, k0+kb:d]  (L11 unit lower, kb <= 32), one
+// thread per column: the column's kb entries in registers, L11 staged in shared memory
+// and read as broadcasts, substitution by columns of L11 (independent FMAs per step).
+constexpr int kLuTrsmThreads = 32;
+__global__ void __launch_bounds__(kLuTrsmThreads) k_lu_trsm(int d, int k0, int kb, double *A0) {
+  __shared__ double L[32 * 32];
   double *A = A0 + (int64_t)blockIdx.y * d * d;
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int i = e % kb, j = e / kb;
+    L[i + 32 * j] = A[(k0 + i) + (int64_t)(k0 + j) * d];
+  }
+  __syncthreads();
   const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d) return;
-  double *col = A + (int64_t)c * d;
-  for (int i = k0 + 1; i < k0 + kb; ++i) {
-    double s = col[i];
-    for (int l = k0; l < i; ++l) s -= A[i + (int64_t)l * d] * col[l];
-    col[i] = s;
+  double *col = A + (int64_t)c * d + k0;
+  double v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = (i < kb) ? col[i] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 31; ++j) {
+#pragma unroll
+    for (int i = j + 1; i < 32; ++i)
+      if (i < kb) v[i] = fma(-L[i + 32 * j], v[j], v[i]);
   }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < kb) col[i] = v[i];
 }
 
 // ---------------------------------------------------------------- triangular solves
 // X (d x m, ld d) <- op(A)^-1 X with A = P L U packed (LAPACK interchanges), d <= 512.
-// One warp per right-hand side, its vector in registers (element i in lane i % 32, slot
-// i / 32), kSolveWarps right-hand sides per block sharing the factor.  The columns of L
-// and U stream through two shared-memory buffers of kSolveChunk columns: the block
-// copies the next chunk asynchronously (cp.async, no registers held) while it works on
-// the current one, so a step costs a shared-memory read and a shuffle, not an L2 round
-// trip.  L and U are applied by columns; U^T and L^T in dot-product form (a column per
-// step, then a warp sum).  The interchanges go through a per-warp shared-memory copy of
-// the vector.
-constexpr int kSolveSlots = 16;
-constexpr int kSolveWarps = 1;   // one right-hand side per block: the FP64 FMAs spread over SMs
+// One block of four warps per right-hand side; row i of the vector lives in a register of
+// thread i % 128 (slot i / 128), so the FP64 FMAs use all four schedulers of the SM.  The
+// two triangular passes go by chunks of kSolveChunk unknowns: the warp that owns the
+// chunk's rows solves its diagonal block by substitution (a shuffle and an FMA per
+// unknown), then every thread applies the chunk to its rows still to be solved.  The
+// factor streams through two shared-memory buffers, the next chunk copied by cp.async
+// while the current one is applied: a column block of L or U for A, a row block (stride
+// kSolveChunk + 1, against bank conflicts) for A^T.  The diagonal of U enters as
+// reciprocals formed once per launch, so no divide lies on the substitution chain.
+constexpr int kSolveThreads = 128;
+constexpr int kSolveSlots = 4;                 // rows per thread: i = s * 128 + threadIdx.x
 constexpr int kSolveChunk = 16;
+constexpr int kSolveLdT = kSolveChunk + 1;
 __device__ __forceinline__ double slot_get(const double (&v)[kSolveSlots], int s) {
   double r = 0.0;
 #pragma unroll
@@ -353,18 +397,8 @@ __device__ __forceinline__ void slot_set(double (&v)[kSolveSlots], int s, double
 #pragma unroll
   for (int t = 0; t < kSolveSlots; ++t) v[t] = (t == s) ? x : v[t];
 }
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
 __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(double *dst, const double *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
                "l"(src)
                : "memory");
 }
@@ -374,143 +408,142 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__global__ void __launch_bounds__(32 * kSolveWarps) k_lu_solve(int d, int m, const double *__restrict__ LU,
-                                                               const int32_t *__restrict__ piv, double *X,
-                                                               int trans) {
+__global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double *__restrict__ LU,
+                                                            const int32_t *__restrict__ piv, double *X, int trans) {
   extern __shared__ __align__(16) double sm[];
-  double *cols = sm;                                   // two buffers of kSolveChunk columns, ld d
-  double *xs = sm + (size_t)2 * kSolveChunk * d + (size_t)(threadIdx.x >> 5) * d;
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kSolveWarps + (threadIdx.x >> 5);
-  const bool active = c < m;                           // idle warps still copy columns
-  double *x = X + (int64_t)(active ? c : 0) * d;
-  double v[kSolveSlots];
+  const int bufsz = kSolveLdT * d;
+  double *xs = sm + 2 * (size_t)bufsz;                 // the vector, for the interchanges
+  double *xc = xs + d;                                 // two chunks of solved unknowns
+  int32_t *ps = reinterpret_cast<int32_t *>(xc + 2 * kSolveChunk);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double *x = X + (int64_t)blockIdx.x * d;
   const int nchunk = (d + kSolveChunk - 1) / kSolveChunk;
-  // chunk-steps 0 .. 2 nchunk - 1: first pass ascending, second pass descending
+  // chunk-steps 0 .. 2 nchunk - 1: the first pass ascends (forward), the second descends
   auto chunk_of = [&](int k) { return k < nchunk ? k : 2 * nchunk - 1 - k; };
-  const bool wide = ((d & 1) == 0) && ((reinterpret_cast<uintptr_t>(LU) & 15) == 0);
-  // copy columns [j0, j0 + kSolveChunk) of LU (contiguous) into buffer b
-  auto issue = [&](int ch, int b) {
-    const int j0 = ch * kSolveChunk;
-    const int total = min(kSolveChunk, d - j0) * d;
-    const double *src = LU + (int64_t)j0 * d;
-    double *dst = cols + (size_t)b * kSolveChunk * d;
-    if (wide) {
-      for (int e = 2 * (int)threadIdx.x; e < total; e += 2 * (int)blockDim.x) cp_async16(dst + e, src + e);
-    } else {
-      for (int e = threadIdx.x; e < total; e += blockDim.x) cp_async8(dst + e, src + e);
+  auto issue = [&](int k) {
+    const int j0 = chunk_of(k) * kSolveChunk;
+    const int w = min(kSolveChunk, d - j0);
+    const bool fwd = k < nchunk;
+    double *dst = sm + (size_t)(k & 1) * bufsz;
+    if (!trans) {      // columns j0 .. j0+w of L (rows j0..d) or U (rows 0..j0+w)
+      const int lo = fwd ? j0 : 0, hi = fwd ? d : j0 + w;
+      for (int jj = 0; jj < w; ++jj)
+        for (int r = lo + tid; r < hi; r += kSolveThreads)
+          cp_async8(dst + (size_t)jj * d + r, LU + (int64_t)(j0 + jj) * d + r);
+    } else {           // rows j0 .. j0+w of U (columns j0..d) or L (columns 0..j0+w)
+      const int lo = fwd ? j0 : 0, hi = fwd ? d : j0 + w;
+      for (int e = tid; e < (hi - lo) * kSolveChunk; e += kSolveThreads) {
+        const int i = lo + (e >> 4), jj = e & (kSolveChunk - 1);
+        if (jj < w) cp_async8(dst + (size_t)i * kSolveLdT + jj, LU + (int64_t)i * d + j0 + jj);
+      }
     }
     cp_async_commit();
   };
-  auto swaps = [&](bool forward) {
-    if (lane == 0 && active) {
-      if (forward) {
-        for (int j = 0; j < d; ++j) {
-          int p = piv[j];
-          if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
-        }
-      } else {
-        for (int j = d - 1; j >= 0; --j) {
-          int p = piv[j];
-          if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
-        }
-      }
+  issue(0);
+  for (int i = tid; i < d; i += kSolveThreads) {
+    ps[i] = piv[i];
+    xs[i] = x[i];
+  }
+  __syncthreads();
+  if (!trans && tid == 0) {
+    for (int j = 0; j < d; ++j) {
+      const int p = ps[j];
+      if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
     }
-    __syncwarp();
-  };
-  issue(0, 0);
-  if (!trans) {
-    if (active) for (int i = lane; i < d; i += 32) xs[i] = x[i];
-    __syncwarp();
-    swaps(true);
+  }
+  __syncthreads();
+  double v[kSolveSlots], rd[kSolveSlots];
 #pragma unroll
-    for (int s = 0; s < kSolveSlots; ++s) v[s] = (s * 32 + lane < d) ? xs[s * 32 + lane] : 0.0;
-  } else {
-#pragma unroll
-    for (int s = 0; s < kSolveSlots; ++s) v[s] = (active && s * 32 + lane < d) ? x[s * 32 + lane] : 0.0;
+  for (int s = 0; s < kSolveSlots; ++s) {
+    const int i = s * kSolveThreads + tid;
+    v[s] = i < d ? xs[i] : 0.0;
+    rd[s] = i < d ? 1.0 / LU[(int64_t)i * d + i] : 0.0;
   }
   for (int k = 0; k < 2 * nchunk; ++k) {
     if (k + 1 < 2 * nchunk) {
-      issue(chunk_of(k + 1), (k + 1) & 1);
+      issue(k + 1);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const double *cb = cols + (size_t)(k & 1) * kSolveChunk * d;
-    const int ch = chunk_of(k);
-    const int j0 = ch * kSolveChunk, j1 = min(d, j0 + kSolveChunk);
-    if (!trans) {
-      if (k < nchunk) {
-        for (int j = j0; j < j1; ++j) {                // L y = P x  (unit lower), by columns
-          const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31);
-          const double *col = cb + (size_t)(j - j0) * d;
-#pragma unroll
-          for (int s = 0; s < kSolveSlots; ++s) {
-            if (s * 32 + 31 <= j || s * 32 >= d) continue;   // no active row in this slot
-            const int i = s * 32 + lane;
-            if (i > j && i < d) v[s] = fma(-col[i], xj, v[s]);
-          }
-        }
-      } else {
-        for (int j = j1 - 1; j >= j0; --j) {           // U x = y, by columns
-          const double *col = cb + (size_t)(j - j0) * d;
-          const double xj = __shfl_sync(0xffffffffu, slot_get(v, j >> 5), j & 31) / col[j];
-          if (lane == (j & 31)) slot_set(v, j >> 5, xj);
-#pragma unroll
-          for (int s = 0; s < kSolveSlots; ++s) {
-            if (s * 32 >= j) continue;
-            const int i = s * 32 + lane;
-            if (i < j) v[s] = fma(-col[i], xj, v[s]);
-          }
-        }
+    const double *cb = sm + (size_t)(k & 1) * bufsz;
+    // op(A)(i, j0 + jj) from the staged block
+    auto opA = [&](int i, int jj) -> double {
+      return trans ? cb[(size_t)i * kSolveLdT + jj] : cb[(size_t)jj * d + i];
+    };
+    const bool fwd = k < nchunk;
+    const bool unit = trans ? !fwd : fwd;      // L and L^T have a unit diagonal
+    const int j0 = chunk_of(k) * kSolveChunk;
+    const int w = min(kSolveChunk, d - j0);
+    double *xck = xc + (k & 1) * kSolveChunk;
+    // 1. diagonal block, by the warp that owns rows j0 .. j0+w (all in one slot)
+    if (warp == ((j0 % kSolveThreads) >> 5)) {
+      const int q0 = j0 / kSolveThreads;
+      const int i = q0 * kSolveThreads + tid;
+      double vq = slot_get(v, q0);
+      const double rq = slot_get(rd, q0);
+      const bool mine = i >= j0 && i < j0 + w;
+      for (int t = 0; t < w; ++t) {
+        const int jj = fwd ? t : w - 1 - t;
+        const int j = j0 + jj;
+        if (!unit && i == j) vq *= rq;
+        const double xj = __shfl_sync(0xffffffffu, vq, j & 31);
+        if (mine && (fwd ? i > j : i < j)) vq = fma(-opA(i, jj), xj, vq);
       }
-    } else {
-      // A^T = U^T L^T P:  U^T z = x (lower), L^T w = z (unit upper), x = P^T w
-      if (k < nchunk) {
-        for (int j = j0; j < j1; ++j) {                // z_j = (x_j - sum_{i<j} U_ij z_i) / U_jj
-          const double *col = cb + (size_t)(j - j0) * d;
-          double part = 0.0;
+      slot_set(v, q0, vq);
+      if (mine) xck[i - j0] = vq;
+    }
+    __syncthreads();
+    // 2. the chunk applied to the rows still to be solved
 #pragma unroll
-          for (int s = 0; s < kSolveSlots; ++s) {
-            if (s * 32 >= j) continue;
-            const int i = s * 32 + lane;
-            if (i < j) part = fma(col[i], v[s], part);
-          }
-          const double tot = warp_sum(part);
-          if (lane == (j & 31)) slot_set(v, j >> 5, (slot_get(v, j >> 5) - tot) / col[j]);
-        }
-      } else {
-        for (int j = j1 - 1; j >= j0; --j) {           // w_j = z_j - sum_{i>j} L_ij w_i
-          const double *col = cb + (size_t)(j - j0) * d;
-          double part = 0.0;
+    for (int s = 0; s < kSolveSlots; ++s) {
+      const int i = s * kSolveThreads + tid;
+      if (fwd ? (i >= j0 + w && i < d) : (i < j0)) {
+        double a = v[s];
+        if (w == kSolveChunk) {
 #pragma unroll
-          for (int s = 0; s < kSolveSlots; ++s) {
-            if (s * 32 + 31 <= j || s * 32 >= d) continue;
-            const int i = s * 32 + lane;
-            if (i > j && i < d) part = fma(col[i], v[s], part);
+          for (int t = 0; t < kSolveChunk; ++t) {
+            const int jj = fwd ? t : kSolveChunk - 1 - t;
+            a = fma(-opA(i, jj), xck[jj], a);
           }
-          const double tot = warp_sum(part);
-          if (lane == (j & 31)) slot_set(v, j >> 5, slot_get(v, j >> 5) - tot);
+        } else {
+          for (int t = 0; t < w; ++t) {
+            const int jj = fwd ? t : w - 1 - t;
+            a = fma(-opA(i, jj), xck[jj], a);
+          }
         }
+        v[s] = a;
       }
     }
     __syncthreads();                                   // buffer k & 1 is refilled at step k + 2
   }
   if (!trans) {
-    if (active) {
 #pragma unroll
-      for (int s = 0; s < kSolveSlots; ++s)
-        if (s * 32 + lane < d) x[s * 32 + lane] = v[s];
+    for (int s = 0; s < kSolveSlots; ++s) {
+      const int i = s * kSolveThreads + tid;
+      if (i < d) x[i] = v[s];
     }
   } else {
 #pragma unroll
-    for (int s = 0; s < kSolveSlots; ++s)
-      if (s * 32 + lane < d) xs[s * 32 + lane] = v[s];
-    __syncwarp();
-    swaps(false);
-    if (active) for (int i = lane; i < d; i += 32) x[i] = xs[i];
+    for (int s = 0; s < kSolveSlots; ++s) {
+      const int i = s * kSolveThreads + tid;
+      if (i < d) xs[i] = v[s];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = d - 1; j >= 0; --j) {
+        const int p = ps[j];
+        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < d; i += kSolveThreads) x[i] = xs[i];
   }
+}
+
+static size_t lu_solve_smem(int d) {
+  return sizeof(double) * ((size_t)2 * kSolveLdT * d + d + 2 * kSolveChunk) + sizeof(int32_t) * (size_t)d;
 }
 
 // C (d x m) = op(A) (d x d) * Bm (d x m), FP64, ld = d.  transA: C = A^T B.
@@ -671,7 +704,7 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
     const int rest = d - k0 - kb;
     if (rest <= 0) continue;
     note_launch();
-    k_lu_trsm<<<dim3((unsigned)ceil_div(rest, 128), nmat), 128, 0, st>>>(d, k0, kb, A);
+    k_lu_trsm<<<dim3((unsigned)ceil_div(rest, kLuTrsmThreads), nmat), kLuTrsmThreads, 0, st>>>(d, k0, kb, A);
     CK_CUDA(cudaGetLastError());
     double *L21 = A + (k0 + kb) + (int64_t)k0 * d;
     double *U12 = A + k0 + (int64_t)(k0 + kb) * d;
@@ -682,12 +715,11 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
 }
 
 static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
-  if (d > 32 * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
-  const size_t smem = sizeof(double) * (size_t)(2 * kSolveChunk + kSolveWarps) * d;
+  if (d > kSolveThreads * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
+  if (m <= 0 || d <= 0) return ok();
   CK_CUDA(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(double) * (2 * kSolveChunk + kSolveWarps) * 512)));
-  ::ckinv::note_launch(), k_lu_solve<<<(unsigned)ceil_div(m, kSolveWarps), 32 * kSolveWarps, smem, st>>>(d, m, LU, piv,
-                                                                                                       X, trans);
+                               (int)lu_solve_smem(kSolveThreads * kSolveSlots)));
+  ::ckinv::note_launch(), k_lu_solve<<<(unsigned)m, kSolveThreads, lu_solve_smem(d), st>>>(d, LU, piv, X, trans);
   CK_CUDA(cudaGetLastError());
   return ok();
 }

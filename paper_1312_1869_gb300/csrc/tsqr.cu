@@ -299,36 +299,49 @@ Error axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta
 // ---------------------------------------------------------------- tree combine panels
 // Householder QR of stacked pairs S = [R_a; R_b] (2d x d, ld 2d, both blocks upper
 // triangular) in panels of sq_nb(T) columns.  Reflector j is e_j on top and v_j (rows
-// 0..j) below, so only the top row j and the bottom rows 0..j take part.  One CTA per
-// combine factors a panel in shared memory (k_sq_panel: every dot product of a step in one
-// pass, one warp per column); the trailing columns and the off-diagonal blocks of the
-// compact-WY factor T are batched GEMMs over all combines of the level (sq_factor).
+// 0..j) below, so only the top row j and the bottom rows 0..j take part.  Per panel there
+// is one launch over all combines of the level (k_sq_step), its CTAs in four roles:
+//   panel:  apply the previous panel's block reflector to this panel's columns, then
+//           factor the panel in shared memory (every dot product of a step in one pass,
+//           one warp per column);
+//   update: apply the previous panel's block reflector to the columns after this panel
+//           (W = C_top + V^T C_bot, W2 = T_kk^T W, C_top -= W2, C_bot -= V W2);
+//   S:      S = V_bot[:, 0:jp]^T V_jp for the previous panel jp;
+//   T:      T[0:jq, panel jq] = -T[0:jq, 0:jq] S T_kk for the panel before that.
+// The next panel thus waits on one launch only: it finishes its own columns' update from
+// the panel before it (lookahead), while the rest of that update, the S products and the
+// T blocks run beside it on other SMs.
 template <typename T>
 constexpr int sq_nb() { return sizeof(T) == 4 ? 32 : 16; }
 constexpr int SQ_THREADS = 512;
 
 template <typename T>
-size_t sq_panel_smem(int d) {
-  constexpr int NBS = sq_nb<T>();
-  return sizeof(T) * ((size_t)d * NBS + 2 * NBS * NBS + 2 * NBS + 4);
+size_t sq_step_smem(int d) {
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
+  const size_t pan = (size_t)NBS * d + (size_t)d * LD + 4 * NBS * LD + 2 * NBS * NBS + 2 * NBS + 4;
+  const size_t upd = (size_t)2 * d * LD + 4 * NBS * LD;
+  return sizeof(T) * std::max(pan, upd);
 }
 
-// Panel [j0, j0 + nb) of every combine: R rows into the top of S, V_bot columns into rows
-// d..2d-1 of Vx (zeros below each reflector), the panel's T block into Tm's diagonal.
+// Panel [j0, j0 + nb): R rows into the top of S, V_bot columns into rows d..2d-1 of Vx
+// (zeros below each reflector), the panel's T block into Tm's diagonal.  For j0 > 0 the
+// previous panel's reflector is first applied to the panel's columns (its top rows are
+// written back; the bottom rows stay in shared memory and are factored).
 template <typename T>
-__global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, int d, int j0) {
-  constexpr int NBS = sq_nb<T>();
+__device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
   constexpr int NW = SQ_THREADS / 32;
-  extern __shared__ __align__(16) uint8_t sm_raw[];
-  T *Vp = reinterpret_cast<T *>(sm_raw);          // NBS columns x d rows: the panel's bottom part
-  T *Ct = Vp + (size_t)NBS * d;                   // NBS x NBS top block, row-major
+  T *Vp = sm;                                     // NBS columns x d rows: the panel's bottom part
+  T *Vq = Vp + (size_t)NBS * d;                   // d x LD: the previous panel's V_bot, row-major
+  T *Ctp = Vq + (size_t)d * LD;                   // NBS x LD: previous panel's top rows of these columns
+  T *Tkp = Ctp + NBS * LD;                        // NBS x LD: previous panel's T_kk
+  T *W = Tkp + NBS * LD;
+  T *W2 = W + NBS * LD;
+  T *Ct = W2 + NBS * LD;                          // NBS x NBS top block, row-major
   T *Tk = Ct + NBS * NBS;                         // NBS x NBS panel T, row-major
   T *Dt = Tk + NBS * NBS;                         // NBS raw dots of the current step
   T *Ih = Dt + NBS;                               // 1 / head of each reflector (Vp keeps x unscaled)
   const int H = 2 * d;
-  T *M = M0 + (int64_t)blockIdx.x * H * d;
-  T *Vx = Vx0 + (int64_t)blockIdx.x * H * d;
-  T *Tm = Tm0 + (int64_t)blockIdx.x * d * d;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = min(NBS, d - j0);
   const int rows = j0 + nb;                       // bottom rows the panel touches
@@ -337,6 +350,53 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
     const int r = e / NBS, c = e % NBS;
     Ct[e] = (r < nb && c < nb) ? M[j0 + r + (int64_t)(j0 + c) * H] : T(0);
     Tk[e] = T(0);
+  }
+  if (j0 > 0) {
+    const int jp = j0 - NBS;                      // full width; its reflectors use bottom rows 0..j0-1
+    stage_tile<T, 8>(Vq, LD, 1, Vx + d + (int64_t)jp * H, H, j0, NBS, NBS);
+    for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
+      const int r = e % NBS, c = e / NBS;
+      Ctp[r * LD + c] = (c < nb) ? M[jp + r + (int64_t)(j0 + c) * H] : T(0);
+      Tkp[r * LD + c] = Tm[(jp + r) + (int64_t)(jp + c) * d];
+    }
+    __syncthreads();
+    // W = C_top + V^T C_bot  (r: previous reflector, c: this panel's column)
+    for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
+      const int r = e % NBS, c = e / NBS;
+      if (c >= nb) {
+        W[r * LD + c] = T(0);
+        continue;
+      }
+      const T *y = Vp + (size_t)c * d;
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
+      int i = 0;
+      for (; i + 4 <= j0; i += 4) {
+        a0 += Vq[i * LD + r] * y[i];
+        a1 += Vq[(i + 1) * LD + r] * y[i + 1];
+        a2 += Vq[(i + 2) * LD + r] * y[i + 2];
+        a3 += Vq[(i + 3) * LD + r] * y[i + 3];
+      }
+      for (; i < j0; ++i) a0 += Vq[i * LD + r] * y[i];
+      W[r * LD + c] = Ctp[r * LD + c] + ((a0 + a1) + (a2 + a3));
+    }
+    __syncthreads();
+    // W2 = T_kk^T W ; C_top -= W2
+    for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
+      const int c = e % NBS, r = e / NBS;
+      T acc = 0;
+      for (int k = 0; k <= r; ++k) acc += Tkp[k * LD + r] * W[k * LD + c];
+      W2[r * LD + c] = acc;
+      if (c < nb) M[jp + r + (int64_t)(j0 + c) * H] = Ctp[r * LD + c] - acc;
+    }
+    __syncthreads();
+    // C_bot -= V W2 on bottom rows 0..j0-1
+    for (int e = tid; e < j0 * nb; e += SQ_THREADS) {
+      const int i = e % j0, c = e / j0;
+      T acc = 0;
+#pragma unroll 8
+      for (int r = 0; r < NBS; ++r) acc += Vq[i * LD + r] * W2[r * LD + c];
+      Vp[(size_t)c * d + i] -= acc;
+    }
   }
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
@@ -403,122 +463,110 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_panel(T *M0, T *Vx0, T *Tm0, 
       Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] * Ih[c] : T(0);
 }
 
-// After panel [j0, j0 + nb) of every combine, one launch does the rest of the panel's work:
-// CTAs 0 .. ceil(nt / NBS) - 1 apply the panel's block reflector to NBS trailing columns
-// each (W = C_top + V^T C_bot, W2 = T_kk^T W, C_top -= W2, C_bot -= V W2, all in shared
-// memory), and the remaining CTAs compute NBS rows each of S = V_bot[:, 0:j0]^T V_panel for
-// the panel's block of T (finished by k_sq_tblock).  V_panel and C_bot use rows 0..j0+nb-1.
+// Panel jp's block reflector applied to NBS columns from cb (V_panel and C_bot use
+// bottom rows 0..jp+nb-1).
 template <typename T>
-size_t sq_update_smem(int d) {
-  constexpr int NBS = sq_nb<T>();
-  return sizeof(T) * ((size_t)2 * d * (NBS + 1) + 4 * NBS * (NBS + 1));
-}
-
-template <typename T>
-__global__ void __launch_bounds__(SQ_THREADS) k_sq_update(T *M0, const T *Vx0, const T *Tm0, T *S0, int d, int j0) {
-  constexpr int NBS = sq_nb<T>();
-  constexpr int LD = NBS + 1;                     // padded rows of the shared tiles
-  extern __shared__ __align__(16) uint8_t sm_raw[];
-  T *Vs = reinterpret_cast<T *>(sm_raw);          // rows x NBS: the panel's V_bot
-  T *Cs = Vs + (size_t)d * LD;                    // rows x NBS: C_bot tile, or V_bot[:, l0..] for S
+__device__ void sq_update_role(T *sm, T *M, const T *Vx, const T *Tm, int d, int jp, int cb) {
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
+  T *Vs = sm;                                     // rows x NBS: the panel's V_bot
+  T *Cs = Vs + (size_t)d * LD;                    // rows x NBS: C_bot tile
   T *Ctp = Cs + (size_t)d * LD;                   // NBS x NBS: C_top tile
   T *Tk = Ctp + NBS * LD;                         // NBS x NBS: T_kk
-  T *W = Tk + NBS * LD;                           // NBS x NBS
+  T *W = Tk + NBS * LD;
   T *W2 = W + NBS * LD;
   const int H = 2 * d;
-  const int nb = min(NBS, d - j0), rows = j0 + nb, c1 = rows, nt = d - c1;
-  const int ntile = (nt + NBS - 1) / NBS;
-  T *M = M0 + (int64_t)blockIdx.y * H * d;
-  const T *Vx = Vx0 + (int64_t)blockIdx.y * H * d;
-  const T *Tm = Tm0 + (int64_t)blockIdx.y * d * d;
-  T *S = S0 + (int64_t)blockIdx.y * d * NBS;      // j0 x nb, ld d
+  const int nb = min(NBS, d - jp), rows = jp + nb;
+  const int nc = min(NBS, d - cb);
   const int tid = threadIdx.x;
-  stage_tile<T, 8>(Vs, LD, 1, Vx + d + (int64_t)j0 * H, H, rows, NBS, nb);
-  if ((int)blockIdx.x < ntile) {
-    const int cb = c1 + blockIdx.x * NBS;
-    const int nc = min(NBS, d - cb);
-    stage_tile<T, 8>(Cs, LD, 1, M + d + (int64_t)cb * H, H, rows, NBS, nc);
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int r = e % NBS, cc = e / NBS;
-      Ctp[r * LD + cc] = (r < nb && cc < nc) ? M[j0 + r + (int64_t)(cb + cc) * H] : T(0);
-      Tk[r * LD + cc] = (r < nb && cc < nb) ? Tm[(j0 + r) + (int64_t)(j0 + cc) * d] : T(0);
+  stage_tile<T, 8>(Vs, LD, 1, Vx + d + (int64_t)jp * H, H, rows, NBS, nb);
+  stage_tile<T, 8>(Cs, LD, 1, M + d + (int64_t)cb * H, H, rows, NBS, nc);
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int r = e % NBS, cc = e / NBS;
+    Ctp[r * LD + cc] = (r < nb && cc < nc) ? M[jp + r + (int64_t)(cb + cc) * H] : T(0);
+    Tk[r * LD + cc] = (r < nb && cc < nb) ? Tm[(jp + r) + (int64_t)(jp + cc) * d] : T(0);
+  }
+  __syncthreads();
+  // W = C_top + V^T C_bot
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int cc = e % NBS, r = e / NBS;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
+    int i = 0;
+    for (; i + 4 <= rows; i += 4) {
+      a0 += Vs[i * LD + r] * Cs[i * LD + cc];
+      a1 += Vs[(i + 1) * LD + r] * Cs[(i + 1) * LD + cc];
+      a2 += Vs[(i + 2) * LD + r] * Cs[(i + 2) * LD + cc];
+      a3 += Vs[(i + 3) * LD + r] * Cs[(i + 3) * LD + cc];
     }
-    __syncthreads();
-    // W = C_top + V^T C_bot
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int cc = e % NBS, r = e / NBS;
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
-      int i = 0;
-      for (; i + 4 <= rows; i += 4) {
-        a0 += Vs[i * LD + r] * Cs[i * LD + cc];
-        a1 += Vs[(i + 1) * LD + r] * Cs[(i + 1) * LD + cc];
-        a2 += Vs[(i + 2) * LD + r] * Cs[(i + 2) * LD + cc];
-        a3 += Vs[(i + 3) * LD + r] * Cs[(i + 3) * LD + cc];
-      }
-      for (; i < rows; ++i) a0 += Vs[i * LD + r] * Cs[i * LD + cc];
-      W[r * LD + cc] = Ctp[r * LD + cc] + ((a0 + a1) + (a2 + a3));
-    }
-    __syncthreads();
-    // W2 = T_kk^T W ; C_top -= W2
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int cc = e % NBS, r = e / NBS;
-      T acc = 0;
-      for (int k = 0; k <= r; ++k) acc += Tk[k * LD + r] * W[k * LD + cc];
-      W2[r * LD + cc] = acc;
-      if (r < nb && cc < nc) M[j0 + r + (int64_t)(cb + cc) * H] = Ctp[r * LD + cc] - acc;
-    }
-    __syncthreads();
-    // C_bot -= V W2
-    for (int e = tid; e < rows * NBS; e += blockDim.x) {
-      const int cc = e % NBS, i = e / NBS;
-      if (cc >= nc) continue;
-      T acc = 0;
+    for (; i < rows; ++i) a0 += Vs[i * LD + r] * Cs[i * LD + cc];
+    W[r * LD + cc] = Ctp[r * LD + cc] + ((a0 + a1) + (a2 + a3));
+  }
+  __syncthreads();
+  // W2 = T_kk^T W ; C_top -= W2
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int cc = e % NBS, r = e / NBS;
+    T acc = 0;
+    for (int k = 0; k <= r; ++k) acc += Tk[k * LD + r] * W[k * LD + cc];
+    W2[r * LD + cc] = acc;
+    if (r < nb && cc < nc) M[jp + r + (int64_t)(cb + cc) * H] = Ctp[r * LD + cc] - acc;
+  }
+  __syncthreads();
+  // C_bot -= V W2
+  for (int e = tid; e < rows * NBS; e += blockDim.x) {
+    const int cc = e % NBS, i = e / NBS;
+    if (cc >= nc) continue;
+    T acc = 0;
 #pragma unroll 8
-      for (int r = 0; r < NBS; ++r) acc += Vs[i * LD + r] * W2[r * LD + cc];
-      M[d + i + (int64_t)(cb + cc) * H] = Cs[i * LD + cc] - acc;
-    }
-  } else {
-    const int l0 = (blockIdx.x - ntile) * NBS;
-    const int nl = min(NBS, j0 - l0);
-    stage_tile<T, 8>(Cs, LD, 1, Vx + d + (int64_t)l0 * H, H, rows, NBS, nl);
-    __syncthreads();
-    // S[l0 + ll][c] = V_bot[:, l0 + ll] . V_panel[:, c]  (rows 0..l0+ll carry V_bot)
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int c = e % NBS, ll = e / NBS;
-      if (ll >= nl || c >= nb) continue;
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      const int imax = min(rows, l0 + ll + 1);
-      int i = 0;
-      for (; i + 4 <= imax; i += 4) {
-        a0 += Cs[i * LD + ll] * Vs[i * LD + c];
-        a1 += Cs[(i + 1) * LD + ll] * Vs[(i + 1) * LD + c];
-        a2 += Cs[(i + 2) * LD + ll] * Vs[(i + 2) * LD + c];
-        a3 += Cs[(i + 3) * LD + ll] * Vs[(i + 3) * LD + c];
-      }
-      for (; i < imax; ++i) a0 += Cs[i * LD + ll] * Vs[i * LD + c];
-      S[(l0 + ll) + (int64_t)c * d] = (a0 + a1) + (a2 + a3);
-    }
+    for (int r = 0; r < NBS; ++r) acc += Vs[i * LD + r] * W2[r * LD + cc];
+    M[d + i + (int64_t)(cb + cc) * H] = Cs[i * LD + cc] - acc;
   }
 }
 
-// T[r][panel] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for rows r of block blockIdx.x (< j0).
+// NBS rows from l0 of S = V_bot[:, 0:jp]^T V_panel for panel jp (S: jp x nb, ld d).
 template <typename T>
-__global__ void __launch_bounds__(SQ_THREADS) k_sq_tblock(T *Tm0, const T *S0, int d, int j0) {
-  constexpr int NBS = sq_nb<T>();
-  constexpr int LD = NBS + 1;
-  __shared__ T Tt[NBS * LD], Sb[NBS * LD], U[NBS * LD], Tk[NBS * LD];
-  const int nb = min(NBS, d - j0);
-  T *Tm = Tm0 + (int64_t)blockIdx.y * d * d;
-  const T *S = S0 + (int64_t)blockIdx.y * d * NBS;
-  const int r0 = blockIdx.x * NBS, nr = min(NBS, j0 - r0);
+__device__ void sq_s_role(T *sm, const T *Vx, T *S, int d, int jp, int l0) {
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
+  T *Vs = sm;
+  T *Cs = Vs + (size_t)d * LD;
+  const int H = 2 * d;
+  const int nb = min(NBS, d - jp), rows = jp + nb;
+  const int nl = min(NBS, jp - l0);
+  const int tid = threadIdx.x;
+  stage_tile<T, 8>(Vs, LD, 1, Vx + d + (int64_t)jp * H, H, rows, NBS, nb);
+  stage_tile<T, 8>(Cs, LD, 1, Vx + d + (int64_t)l0 * H, H, rows, NBS, nl);
+  __syncthreads();
+  // S[l0 + ll][c] = V_bot[:, l0 + ll] . V_panel[:, c]  (rows 0..l0+ll carry V_bot)
+  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+    const int c = e % NBS, ll = e / NBS;
+    if (ll >= nl || c >= nb) continue;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int imax = min(rows, l0 + ll + 1);
+    int i = 0;
+    for (; i + 4 <= imax; i += 4) {
+      a0 += Cs[i * LD + ll] * Vs[i * LD + c];
+      a1 += Cs[(i + 1) * LD + ll] * Vs[(i + 1) * LD + c];
+      a2 += Cs[(i + 2) * LD + ll] * Vs[(i + 2) * LD + c];
+      a3 += Cs[(i + 3) * LD + ll] * Vs[(i + 3) * LD + c];
+    }
+    for (; i < imax; ++i) a0 += Cs[i * LD + ll] * Vs[i * LD + c];
+    S[(l0 + ll) + (int64_t)c * d] = (a0 + a1) + (a2 + a3);
+  }
+}
+
+// T[r][panel jq] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for NBS rows from r0 (< jq).
+template <typename T>
+__device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) {
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
+  T *Tt = sm, *Sb = Tt + NBS * LD, *U = Sb + NBS * LD, *Tk = U + NBS * LD;
+  const int nb = min(NBS, d - jq);
+  const int nr = min(NBS, jq - r0);
   const int tid = threadIdx.x;
   for (int e = tid; e < NBS * NBS; e += blockDim.x) {
     const int a = e % NBS, b = e / NBS;
     U[a * LD + b] = 0;
-    Tk[a * LD + b] = (a < nb && b < nb) ? Tm[(j0 + a) + (int64_t)(j0 + b) * d] : T(0);
+    Tk[a * LD + b] = (a < nb && b < nb) ? Tm[(jq + a) + (int64_t)(jq + b) * d] : T(0);
   }
-  for (int l0 = r0; l0 < j0; l0 += NBS) {
-    const int nl = min(NBS, j0 - l0);
+  for (int l0 = r0; l0 < jq; l0 += NBS) {
+    const int nl = min(NBS, jq - l0);
     __syncthreads();
     for (int e = tid; e < NBS * NBS; e += blockDim.x) {
       const int a = e % NBS, b = e / NBS;         // Tt[a][b] = T[r0 + a][l0 + b];  Sb[a][b] = S[l0 + a][b]
@@ -539,8 +587,43 @@ __global__ void __launch_bounds__(SQ_THREADS) k_sq_tblock(T *Tm0, const T *S0, i
     if (a >= nr || c >= nb) continue;
     T acc = 0;
     for (int k = 0; k < NBS; ++k) acc += U[a * LD + k] * Tk[k * LD + c];
-    Tm[(r0 + a) + (int64_t)(j0 + c) * d] = -acc;
+    Tm[(r0 + a) + (int64_t)(jq + c) * d] = -acc;
   }
+}
+
+// Step q of a level (j0 = q NBS), combine blockIdx.y: CTAs [0, nP) factor panel q, the
+// next nU apply panel q-1 to the columns after panel q, the next nS form S for panel q-1
+// (into buffer (q-1) & 1), the rest form T's blocks for panel q-2 (from buffer q & 1).
+template <typename T>
+__global__ void __launch_bounds__(SQ_THREADS) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
+                                                        int nS) {
+  constexpr int NBS = sq_nb<T>();
+  extern __shared__ __align__(16) uint8_t sm_raw[];
+  T *sm = reinterpret_cast<T *>(sm_raw);
+  const int H = 2 * d;
+  const int y = blockIdx.y;
+  T *M = M0 + (int64_t)y * H * d;
+  T *Vx = Vx0 + (int64_t)y * H * d;
+  T *Tm = Tm0 + (int64_t)y * d * d;
+  const int64_t sS = (int64_t)gridDim.y * d * NBS;
+  const int j0 = q * NBS;
+  int b = blockIdx.x;
+  if (b < nP) {
+    sq_panel_role<T>(sm, M, Vx, Tm, d, j0);
+    return;
+  }
+  b -= nP;
+  if (b < nU) {
+    sq_update_role<T>(sm, M, Vx, Tm, d, j0 - NBS, j0 + NBS + b * NBS);
+    return;
+  }
+  b -= nU;
+  if (b < nS) {
+    sq_s_role<T>(sm, Vx, S0 + ((q - 1) & 1) * sS + (int64_t)y * d * NBS, d, j0 - NBS, b * NBS);
+    return;
+  }
+  b -= nS;
+  sq_tblock_role<T>(sm, Tm, S0 + (q & 1) * sS + (int64_t)y * d * NBS, d, j0 - 2 * NBS, b * NBS);
 }
 
 // One stage: P independent QRs of H x d matrices (strided, ld H).
@@ -677,36 +760,29 @@ Error alloc_stage(Stage<T> &s, int P, int H, int d, const std::vector<int> &top,
   return ok();
 }
 
-// Panel by panel over all combines of a level: the panel kernel, then
-//   T[0:j0, panel] = -T[0:j0, 0:j0] (V_bot[:, 0:j0]^T V_panel) T_panel,
-//   W = C_top + V_panel^T C_bot,  W2 = T_panel^T W,  C_top -= W2,  C_bot -= V_panel W2
-// on the trailing columns (rows 0..j0+nb-1 of the bottom block).
-// Panel by panel over all combines of a level: the panel kernel, then one launch for the
-// trailing update and S = V_bot[:, 0:j0]^T V_panel, then the panel's block of T:
-//   T[0:j0, panel] = -T[0:j0, 0:j0] S T_panel.
+// Panel by panel over all combines of a level, one k_sq_step launch per panel plus two
+// that finish the last panels' S products and T blocks.
 template <typename T>
 Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st) {
+  (void)ctx;
   constexpr int NBS = sq_nb<T>();
   const int P = s.P;
-  const size_t psmem = sq_panel_smem<T>(d), usmem = sq_update_smem<T>(d);
-  CK_CUDA(cudaFuncSetAttribute(k_sq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-  CK_CUDA(cudaFuncSetAttribute(k_sq_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
+  const int npan = (d + NBS - 1) / NBS;
+  const size_t smem = sq_step_smem<T>(d);
+  CK_CUDA(cudaFuncSetAttribute(k_sq_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   T *S = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&S, sizeof(T) * (size_t)P * d * NBS, st));
+  CK_CUDA(cudaMallocAsync((void **)&S, sizeof(T) * 2 * (size_t)P * d * NBS, st));
   Error e = ok();
-  for (int j0 = 0; j0 < d && !e.st; j0 += NBS) {
-    const int nb = std::min(NBS, d - j0), nt = d - j0 - nb;
-    const int ntile = (nt + NBS - 1) / NBS, nstile = (j0 + NBS - 1) / NBS;
+  for (int q = 0; q <= npan + 1 && !e.st; ++q) {
+    const int j0 = q * NBS, jp = j0 - NBS, jq = j0 - 2 * NBS;
+    const int nP = q < npan ? 1 : 0;
+    const int nU = (q >= 1 && q < npan) ? (std::max(0, d - j0 - NBS) + NBS - 1) / NBS : 0;
+    const int nS = (q >= 1 && q - 1 < npan && jp > 0) ? (jp + NBS - 1) / NBS : 0;
+    const int nT = (q >= 2 && q - 2 < npan && jq > 0) ? (jq + NBS - 1) / NBS : 0;
+    const int nx = nP + nU + nS + nT;
+    if (nx == 0) continue;
     note_launch();
-    k_sq_panel<T><<<P, SQ_THREADS, psmem, st>>>(s.M, s.Vx, s.Tm, d, j0);
-    if (ntile + nstile > 0) {
-      note_launch();
-      k_sq_update<T><<<dim3((unsigned)(ntile + nstile), (unsigned)P), SQ_THREADS, usmem, st>>>(s.M, s.Vx, s.Tm, S, d, j0);
-    }
-    if (nstile > 0) {
-      note_launch();
-      k_sq_tblock<T><<<dim3((unsigned)nstile, (unsigned)P), SQ_THREADS, 0, st>>>(s.Tm, S, d, j0);
-    }
+    k_sq_step<T><<<dim3((unsigned)nx, (unsigned)P), SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, S, d, q, nP, nU, nS);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
   }
