@@ -134,7 +134,7 @@ class Plan:
     prec: int = FP32
     seed: int = 0
     refine_steps: int = 1
-    tree_fp64_levels: int = 1
+    tree_fp64_levels: int = -1          # every level of the R tree combined in FP64
     leaf_fp64: int = 0
 
     def desc(self):

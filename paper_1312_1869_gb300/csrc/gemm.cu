@@ -1,5 +1,7 @@
 // Strided-batched GEMM on the CUDA cores (FP32 or FP64), column-major:
-//   C_b = alpha * op(A_b) * B_b + beta * C_b,   op(A) = A or A^T,   b = 0 .. batch-1.
+//   C_b = alpha * op(A_b) * B_b + beta * C_b,   op(A) = A or A^T,   b = 0 .. batch-1,
+// with a two-level batch b = b1 + nb1 * b2 (operand offset b1 * s + b2 * s2) for blocks that
+// repeat inside each of several matrices.
 // Used by the blocked Householder QR (trailing updates, compact-WY assembly and the
 // application of Q to a coefficient block).
 //
@@ -18,7 +20,7 @@ template <typename T, int BM, int BN, int TM, int TN_, bool TRANSA>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 : 3)
     k_gemm(int M, int N, int K, T alpha, const T *__restrict__ A, int64_t lda, int64_t sA,
            const T *__restrict__ B, int64_t ldb, int64_t sB, T beta, T *__restrict__ C, int64_t ldc, int64_t sC,
-           int ksplit, T *__restrict__ part) {
+           int ksplit, T *__restrict__ part, int nb1, int64_t sA2, int64_t sB2, int64_t sC2) {
   constexpr int BK = 8;
   constexpr int NTX = BN / TN_, NTY = BM / TM;
   constexpr int NT = NTX * NTY;
@@ -28,13 +30,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 :
   __shared__ __align__(16) T As[2][BK][BM + 4];   // +4: conflict-free transposing stores
   __shared__ __align__(16) T Bs[2][BK][BN + 4];
   const int batch = blockIdx.z / ksplit, split = blockIdx.z % ksplit;
-  A += (int64_t)batch * sA;
-  B += (int64_t)batch * sB;
+  const int b1 = batch % nb1, b2 = batch / nb1;
+  A += (int64_t)b1 * sA + (int64_t)b2 * sA2;
+  B += (int64_t)b1 * sB + (int64_t)b2 * sB2;
   if (ksplit > 1) {   // partial (split, batch) of the workspace: M x N, ld M
     C = part + ((int64_t)split * (gridDim.z / ksplit) + batch) * M * N;
     ldc = M;
   } else {
-    C += (int64_t)batch * sC;
+    C += (int64_t)b1 * sC + (int64_t)b2 * sC2;
   }
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
@@ -137,14 +140,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 :
 // C_b = beta C_b + sum over s (in order) of part[s][b]
 template <typename T>
 __global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, const T *part, T beta, T *C, int64_t ldc,
-                                int64_t sC) {
+                                int64_t sC, int nb1, int64_t sC2) {
   const int64_t per = (int64_t)M * N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per * batch;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t b = e / per, w = e % per;
     T acc = T(0);
     for (int s = 0; s < ksplit; ++s) acc += part[((int64_t)s * batch + b) * per + w];
-    T *c = C + b * sC + (w % M) + (w / M) * ldc;
+    T *c = C + (b % nb1) * sC + (b / nb1) * sC2 + (w % M) + (w / M) * ldc;
     *c = acc + (beta == T(0) ? T(0) : beta * *c);
   }
 }
@@ -152,19 +155,52 @@ __global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, const T *pa
 template <typename T, int BM, int BN, int TM, int TN_>
 void launch_shape(bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda, int64_t sA, const T *B,
                   int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC, int batch, int ksplit,
-                  T *part, cudaStream_t st) {
+                  T *part, int nb1, int64_t sA2, int64_t sB2, int64_t sC2, cudaStream_t st) {
   dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN), (unsigned)(batch * ksplit));
   constexpr int NT = (BM / TM) * (BN / TN_);
   note_launch();
   if (transA)
     k_gemm<T, BM, BN, TM, TN_, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                          sC, ksplit, part);
+                                                          sC, ksplit, part, nb1, sA2, sB2, sC2);
   else
     k_gemm<T, BM, BN, TM, TN_, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                           sC, ksplit, part);
+                                                           sC, ksplit, part, nb1, sA2, sB2, sC2);
 }
 
 }  // namespace
+
+template <typename T>
+Error gemm_simt(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda, int64_t sA,
+                const T *B, int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC, int nb1, int64_t sA2,
+                int64_t sB2, int64_t sC2, int nb2, cudaStream_t st) {
+  const int batch = nb1 * nb2;
+  // tile choice: 128 x 128 (8 x 8 per thread) for large FP32 outputs, else 64 x 64 (4 x 4)
+  const bool big = (sizeof(T) == 4) && M >= 256 && N >= 128;
+  const int bm = big ? 128 : 64, bn = big ? 128 : 64;
+  const int64_t tiles = ceil_div(M, bm) * ceil_div(N, bn) * (int64_t)batch;
+  int ksplit = 1;
+  const int64_t target = 2LL * ctx->sm_count;
+  if (tiles < target && K >= 256) {
+    ksplit = (int)std::min<int64_t>(std::max<int64_t>(1, target / tiles), K / 128);
+    ksplit = std::max(ksplit, 1);
+  }
+  T *part = nullptr;
+  if (ksplit > 1) CK_CUDA(cudaMallocAsync((void **)&part, sizeof(T) * (size_t)M * N * batch * ksplit, st));
+  if (big)
+    launch_shape<T, 128, 128, 8, 8>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
+                                    part, nb1, sA2, sB2, sC2, st);
+  else
+    launch_shape<T, 64, 64, 4, 4>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
+                                  part, nb1, sA2, sB2, sC2, st);
+  if (ksplit > 1) {
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * N * batch, 256), 4096);
+    note_launch();
+    k_splitk_reduce<T><<<g, 256, 0, st>>>(M, N, batch, ksplit, part, beta, C, ldc, sC, nb1, sC2);
+    cudaFreeAsync(part, st);
+  }
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
 
 template <typename T>
 Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
@@ -180,34 +216,25 @@ Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alp
       (double)M * N * (double)K * batch >= 3.0e7)
     return gemm_tc_f32(ctx, transA, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
                        (float)beta, (float *)C, ldc, sC, batch, st);
-  // tile choice: 128 x 128 (8 x 8 per thread) for large FP32 outputs, else 64 x 64 (4 x 4)
-  const bool big = (sizeof(T) == 4) && M >= 256 && N >= 128;
-  const int bm = big ? 128 : 64, bn = big ? 128 : 64;
-  const int64_t tiles = ceil_div(M, bm) * ceil_div(N, bn) * (int64_t)batch;
-  int ksplit = 1;
-  const int64_t target = 2LL * ctx->sm_count;
-  if (tiles < target && K >= 256) {
-    ksplit = (int)std::min<int64_t>(std::max<int64_t>(1, target / tiles), K / 128);
-    ksplit = std::max(ksplit, 1);
-  }
-  T *part = nullptr;
-  if (ksplit > 1) CK_CUDA(cudaMallocAsync((void **)&part, sizeof(T) * (size_t)M * N * batch * ksplit, st));
-  if (big)
-    launch_shape<T, 128, 128, 8, 8>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
-                                    part, st);
-  else
-    launch_shape<T, 64, 64, 4, 4>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
-                                  part, st);
-  if (ksplit > 1) {
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)M * N * batch, 256), 4096);
-    note_launch();
-    k_splitk_reduce<T><<<g, 256, 0, st>>>(M, N, batch, ksplit, part, beta, C, ldc, sC);
-    cudaFreeAsync(part, st);
-  }
-  CK_CUDA(cudaGetLastError());
-  return ok();
+  return gemm_simt<T>(ctx, transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, 0, 0, 0, 1, st);
 }
 
+template <typename T>
+Error gemm_batched2(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
+                    int64_t sA, int64_t sA2, const T *B, int64_t ldb, int64_t sB, int64_t sB2, T beta, T *C,
+                    int64_t ldc, int64_t sC, int64_t sC2, int nb1, int nb2, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || nb1 <= 0 || nb2 <= 0) return ok();
+  if (K <= 0) {
+    if (beta == T(1)) return ok();
+    return fail(CKINV_EINVAL, "gemm_batched2: K = 0 with beta != 1");
+  }
+  return gemm_simt<T>(ctx, transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, nb1, sA2, sB2, sC2, nb2,
+                      st);
+}
+
+template Error gemm_batched2<float>(const ckinv_ctx *, bool, int, int, int, float, const float *, int64_t, int64_t,
+                                    int64_t, const float *, int64_t, int64_t, int64_t, float, float *, int64_t,
+                                    int64_t, int64_t, int, int, cudaStream_t);
 template Error gemm_batched<float>(const ckinv_ctx *, bool, int, int, int, float, const float *, int64_t, int64_t,
                                    const float *, int64_t, int64_t, float, float *, int64_t, int64_t, int,
                                    cudaStream_t);

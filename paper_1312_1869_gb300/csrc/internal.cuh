@@ -189,6 +189,11 @@ template <typename T>
 Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
                    int64_t sA, const T *B, int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC,
                    int batch, cudaStream_t st);
+// Two-level batch on the CUDA cores: b = b1 + nb1 * b2, operand offset b1 * s + b2 * s2.
+template <typename T>
+Error gemm_batched2(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda,
+                    int64_t sA, int64_t sA2, const T *B, int64_t ldb, int64_t sB, int64_t sB2, T beta, T *C,
+                    int64_t ldc, int64_t sC, int64_t sC2, int nb1, int nb2, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- low rank
 // G (d1 x d2, FP64, ld d1) = L^T M over n rows.  L = explicit FP32 (ldl) or, when

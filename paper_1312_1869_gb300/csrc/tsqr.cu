@@ -8,9 +8,12 @@
 // in two down to 16-column panels, which one CTA per problem factors in shared memory with
 // warp-shuffle reductions; everything else - applying the left part's reflectors to the
 // right part and assembling the compact-WY factor T (Q = I - V T V^T) - is batched GEMM.
-// Leaves run in FP32 (or FP64 on request), the top `fp64_levels` tree levels in FP64.
-// Q_hat is formed top-down from the root's coefficient block D = sign(diag R): each stage
-// maps its blocks X to Q [X; 0] = [X; 0] - V (T (V_top^T X)), three batched GEMMs.
+// Leaves run in FP32 (or FP64 on request), the top `fp64_levels` tree levels in FP64; the
+// R factors passed between levels are FP64 throughout.  Q_hat is formed top-down from the
+// root's coefficient block D = sign(diag R): each stage maps its blocks X to
+// Q [X; 0] = [X; 0] - V (T (V_top^T X)), three batched GEMMs, in the leaves' precision (FP64
+// tree levels hand FP32 copies of their reflectors to an FP32 Q_hat: the combine is where
+// FP64 buys accuracy, and an FP64 product on this part costs ~60x an FP32 one).
 #include "internal.cuh"
 
 namespace ckinv {
@@ -258,6 +261,12 @@ __global__ void k_scatter_x(const T *Qs, const int *top, const int *bot, int d, 
   }
 }
 
+// dst = (float) src, n elements.
+__global__ void k_narrow(const double *src, float *dst, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
 // Q_hat rows of leaf p = Qs_p[0:h_p] (FP32 output, ld n).
 template <typename T>
 __global__ void k_leaf_q(const T *Qs, int H, int d, const int64_t *row0, const int *rows, float *Q, int64_t ldq) {
@@ -311,16 +320,43 @@ Error axpby(int m, int n, T alpha, const T *src, int64_t lds, int64_t ss, T beta
 // The next panel thus waits on one launch only: it finishes its own columns' update from
 // the panel before it (lookahead), while the rest of that update, the S products and the
 // T blocks run beside it on other SMs.
+// FP64 panels are narrower: every step of a panel takes a dot product with each of its
+// columns, and FP64 products are what this part has least of.
 template <typename T>
-constexpr int sq_nb() { return sizeof(T) == 4 ? 32 : 16; }
+constexpr int sq_nb() { return sizeof(T) == 4 ? 32 : 8; }
+constexpr int SQ_KC = 64;         // rows of S (and columns of T) per step of a T-block CTA
+
+// Threads that share one of n_out dot products when there are fewer outputs than threads
+// (FP64 tiles: otherwise half the schedulers' FP64 units would idle).
+__host__ __device__ constexpr int sq_split(int n_out) { return n_out >= 512 ? 1 : 512 / n_out; }
+
+// sum_{i < n} f(i) over a group of KS consecutive lanes (part = index in the group), four
+// chains per thread; every lane of the group gets the total.  All 32 lanes must call it.
+template <typename T, int KS, typename F>
+__device__ __forceinline__ T group_dot(int n, int part, F f) {
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int i = part;
+  for (; i + 3 * KS < n; i += 4 * KS) {
+    a0 += f(i);
+    a1 += f(i + KS);
+    a2 += f(i + 2 * KS);
+    a3 += f(i + 3 * KS);
+  }
+  for (; i < n; i += KS) a0 += f(i);
+  T acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = 1; o < KS; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
 constexpr int SQ_THREADS = 512;
 
 template <typename T>
 size_t sq_step_smem(int d) {
   constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
-  const size_t pan = (size_t)NBS * d + (size_t)d * LD + 4 * NBS * LD + 2 * NBS * NBS + 2 * NBS + 4;
+  const size_t pan = (size_t)NBS * d + (size_t)d * LD + 4 * NBS * LD + 2 * NBS * NBS + 3 * NBS + 4;
   const size_t upd = (size_t)2 * d * LD + 4 * NBS * LD;
-  return sizeof(T) * std::max(pan, upd);
+  const size_t tbl = (size_t)NBS * (SQ_KC + 1) + (size_t)SQ_KC * LD + 2 * NBS * LD;
+  return sizeof(T) * std::max(std::max(pan, upd), tbl);
 }
 
 // Panel [j0, j0 + nb): R rows into the top of S, V_bot columns into rows d..2d-1 of Vx
@@ -341,6 +377,7 @@ __device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
   T *Tk = Ct + NBS * NBS;                         // NBS x NBS panel T, row-major
   T *Dt = Tk + NBS * NBS;                         // NBS raw dots of the current step
   T *Ih = Dt + NBS;                               // 1 / head of each reflector (Vp keeps x unscaled)
+  T *Tau = Ih + NBS;                              // tau of the current step
   const int H = 2 * d;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = min(NBS, d - j0);
@@ -361,23 +398,13 @@ __device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
     }
     __syncthreads();
     // W = C_top + V^T C_bot  (r: previous reflector, c: this panel's column)
-    for (int e = tid; e < NBS * NBS; e += SQ_THREADS) {
-      const int r = e % NBS, c = e / NBS;
-      if (c >= nb) {
-        W[r * LD + c] = T(0);
-        continue;
-      }
+    constexpr int KS = sq_split(NBS * NBS);
+    for (int e = tid; e < NBS * NBS * KS; e += SQ_THREADS) {
+      const int o = e / KS, part = e % KS;
+      const int r = o % NBS, c = o / NBS;
       const T *y = Vp + (size_t)c * d;
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
-      int i = 0;
-      for (; i + 4 <= j0; i += 4) {
-        a0 += Vq[i * LD + r] * y[i];
-        a1 += Vq[(i + 1) * LD + r] * y[i + 1];
-        a2 += Vq[(i + 2) * LD + r] * y[i + 2];
-        a3 += Vq[(i + 3) * LD + r] * y[i + 3];
-      }
-      for (; i < j0; ++i) a0 += Vq[i * LD + r] * y[i];
-      W[r * LD + c] = Ctp[r * LD + c] + ((a0 + a1) + (a2 + a3));
+      const T acc = group_dot<T, KS>(c < nb ? j0 : 0, part, [&](int i) { return Vq[i * LD + r] * y[i]; });
+      if (part == 0) W[r * LD + c] = (c < nb) ? Ctp[r * LD + c] + acc : T(0);
     }
     __syncthreads();
     // W2 = T_kk^T W ; C_top -= W2
@@ -415,20 +442,29 @@ __device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
       T acc = a0 + a1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) Dt[c] = acc;
+      if (lane == 0) {
+        Dt[c] = acc;
+        if (c == jj) {                            // this step's reflector, formed once
+          const T alpha = Ct[jj * NBS + jj];
+          const T sig = acc;
+          const T normx = sqrt(alpha * alpha + sig);
+          T tau = 0, rd = alpha, inv_head = 0;
+          if (normx > T(0) && sig > T(0)) {
+            const T sgn = alpha >= T(0) ? T(1) : T(-1);
+            const T head = alpha + sgn * normx;
+            inv_head = T(1) / head;
+            tau = T(2) / (T(1) + sig * inv_head * inv_head);
+            rd = -sgn * normx;
+          }
+          Ct[jj * NBS + jj] = rd;                 // read by no other thread this step
+          Tk[jj * NBS + jj] = tau;
+          Ih[jj] = inv_head;
+          Tau[0] = tau;
+        }
+      }
     }
     __syncthreads();
-    const T alpha = Ct[jj * NBS + jj];
-    const T sig = Dt[jj];
-    const T normx = sqrt(alpha * alpha + sig);
-    T tau = 0, rd = alpha, inv_head = 0;
-    if (normx > T(0) && sig > T(0)) {
-      const T sgn = alpha >= T(0) ? T(1) : T(-1);
-      const T head = alpha + sgn * normx;
-      inv_head = T(1) / head;
-      tau = T(2) / (T(1) + sig * inv_head * inv_head);
-      rd = -sgn * normx;
-    }
+    const T tau = Tau[0], inv_head = Ih[jj];
     // the rest of the panel: w_c = Ct[jj][c] + (x . col_c) / head, then the reflection
     for (int c = jj + 1 + wid; c < nb; c += NW) {
       const T w = tau * (Ct[jj * NBS + c] + Dt[c] * inv_head);
@@ -445,11 +481,6 @@ __device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) Tk[r * NBS + jj] = -tau * inv_head * t;
-    }
-    if (tid == 0) {
-      Ct[jj * NBS + jj] = rd;
-      Tk[jj * NBS + jj] = tau;
-      Ih[jj] = inv_head;
     }
     __syncthreads();
   }
@@ -487,18 +518,12 @@ __device__ void sq_update_role(T *sm, T *M, const T *Vx, const T *Tm, int d, int
   }
   __syncthreads();
   // W = C_top + V^T C_bot
-  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-    const int cc = e % NBS, r = e / NBS;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;            // four chains in flight
-    int i = 0;
-    for (; i + 4 <= rows; i += 4) {
-      a0 += Vs[i * LD + r] * Cs[i * LD + cc];
-      a1 += Vs[(i + 1) * LD + r] * Cs[(i + 1) * LD + cc];
-      a2 += Vs[(i + 2) * LD + r] * Cs[(i + 2) * LD + cc];
-      a3 += Vs[(i + 3) * LD + r] * Cs[(i + 3) * LD + cc];
-    }
-    for (; i < rows; ++i) a0 += Vs[i * LD + r] * Cs[i * LD + cc];
-    W[r * LD + cc] = Ctp[r * LD + cc] + ((a0 + a1) + (a2 + a3));
+  constexpr int KS = sq_split(NBS * NBS);
+  for (int e = tid; e < NBS * NBS * KS; e += blockDim.x) {
+    const int o = e / KS, part = e % KS;
+    const int cc = o % NBS, r = o / NBS;
+    const T acc = group_dot<T, KS>(rows, part, [&](int i) { return Vs[i * LD + r] * Cs[i * LD + cc]; });
+    if (part == 0) W[r * LD + cc] = Ctp[r * LD + cc] + acc;
   }
   __syncthreads();
   // W2 = T_kk^T W ; C_top -= W2
@@ -535,28 +560,26 @@ __device__ void sq_s_role(T *sm, const T *Vx, T *S, int d, int jp, int l0) {
   stage_tile<T, 8>(Cs, LD, 1, Vx + d + (int64_t)l0 * H, H, rows, NBS, nl);
   __syncthreads();
   // S[l0 + ll][c] = V_bot[:, l0 + ll] . V_panel[:, c]  (rows 0..l0+ll carry V_bot)
-  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-    const int c = e % NBS, ll = e / NBS;
-    if (ll >= nl || c >= nb) continue;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    const int imax = min(rows, l0 + ll + 1);
-    int i = 0;
-    for (; i + 4 <= imax; i += 4) {
-      a0 += Cs[i * LD + ll] * Vs[i * LD + c];
-      a1 += Cs[(i + 1) * LD + ll] * Vs[(i + 1) * LD + c];
-      a2 += Cs[(i + 2) * LD + ll] * Vs[(i + 2) * LD + c];
-      a3 += Cs[(i + 3) * LD + ll] * Vs[(i + 3) * LD + c];
-    }
-    for (; i < imax; ++i) a0 += Cs[i * LD + ll] * Vs[i * LD + c];
-    S[(l0 + ll) + (int64_t)c * d] = (a0 + a1) + (a2 + a3);
+  constexpr int KS = sq_split(NBS * NBS);
+  for (int e = tid; e < NBS * NBS * KS; e += blockDim.x) {
+    const int o = e / KS, part = e % KS;
+    const int c = o % NBS, ll = o / NBS;
+    const bool valid = ll < nl && c < nb;
+    const int imax = valid ? min(rows, l0 + ll + 1) : 0;
+    const T acc = group_dot<T, KS>(imax, part, [&](int i) { return Cs[i * LD + ll] * Vs[i * LD + c]; });
+    if (valid && part == 0) S[(l0 + ll) + (int64_t)c * d] = acc;
   }
 }
 
-// T[r][panel jq] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for NBS rows from r0 (< jq).
+// T[r][panel jq] = -(sum_{l >= r} T[r][l] S[l][.]) T_kk for NBS rows from r0 (< jq); S and
+// T stream through shared memory SQ_KC rows / columns at a time.
 template <typename T>
 __device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) {
-  constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
-  T *Tt = sm, *Sb = Tt + NBS * LD, *U = Sb + NBS * LD, *Tk = U + NBS * LD;
+  constexpr int NBS = sq_nb<T>(), LD = NBS + 1, LK = SQ_KC + 1;
+  T *Tt = sm;                                     // NBS x LK: T[r0 + a][l0 + b]
+  T *Sb = Tt + NBS * LK;                          // SQ_KC x LD: S[l0 + a][b]   (row-major, ld LD)
+  T *U = Sb + SQ_KC * LD;                         // NBS x LD
+  T *Tk = U + NBS * LD;                           // NBS x LD
   const int nb = min(NBS, d - jq);
   const int nr = min(NBS, jq - r0);
   const int tid = threadIdx.x;
@@ -565,20 +588,24 @@ __device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) 
     U[a * LD + b] = 0;
     Tk[a * LD + b] = (a < nb && b < nb) ? Tm[(jq + a) + (int64_t)(jq + b) * d] : T(0);
   }
-  for (int l0 = r0; l0 < jq; l0 += NBS) {
-    const int nl = min(NBS, jq - l0);
+  for (int l0 = r0; l0 < jq; l0 += SQ_KC) {
+    const int nl = min(SQ_KC, jq - l0);
     __syncthreads();
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int a = e % NBS, b = e / NBS;         // Tt[a][b] = T[r0 + a][l0 + b];  Sb[a][b] = S[l0 + a][b]
-      Tt[a * LD + b] = (a < nr && b < nl) ? Tm[(r0 + a) + (int64_t)(l0 + b) * d] : T(0);
+    for (int e = tid; e < NBS * SQ_KC; e += blockDim.x) {
+      const int a = e % NBS, b = e / NBS;         // T column-major: consecutive a are consecutive rows
+      Tt[a * LK + b] = (a < nr && b < nl) ? Tm[(r0 + a) + (int64_t)(l0 + b) * d] : T(0);
+    }
+    for (int e = tid; e < SQ_KC * NBS; e += blockDim.x) {
+      const int a = e % SQ_KC, b = e / SQ_KC;
       Sb[a * LD + b] = (a < nl && b < nb) ? S[(l0 + a) + (int64_t)b * d] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-      const int c = e % NBS, a = e / NBS;
-      T acc = 0;
-      for (int l = 0; l < NBS; ++l) acc += Tt[a * LD + l] * Sb[l * LD + c];
-      U[a * LD + c] += acc;
+    constexpr int KS = sq_split(NBS * NBS);
+    for (int e = tid; e < NBS * NBS * KS; e += blockDim.x) {
+      const int o = e / KS, part = e % KS;
+      const int c = o % NBS, a = o / NBS;
+      const T acc = group_dot<T, KS>(nl, part, [&](int l) { return Tt[a * LK + l] * Sb[l * LD + c]; });
+      if (part == 0) U[a * LD + c] += acc;
     }
   }
   __syncthreads();
@@ -595,7 +622,7 @@ __device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) 
 // next nU apply panel q-1 to the columns after panel q, the next nS form S for panel q-1
 // (into buffer (q-1) & 1), the rest form T's blocks for panel q-2 (from buffer q & 1).
 template <typename T>
-__global__ void __launch_bounds__(SQ_THREADS) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
+__global__ void __launch_bounds__(SQ_THREADS, sizeof(T) == 8 ? 3 : 1) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
                                                         int nS) {
   constexpr int NBS = sq_nb<T>();
   extern __shared__ __align__(16) uint8_t sm_raw[];
@@ -763,7 +790,7 @@ Error alloc_stage(Stage<T> &s, int P, int H, int d, const std::vector<int> &top,
 // Panel by panel over all combines of a level, one k_sq_step launch per panel plus two
 // that finish the last panels' S products and T blocks.
 template <typename T>
-Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st) {
+Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, bool with_t, cudaStream_t st) {
   (void)ctx;
   constexpr int NBS = sq_nb<T>();
   const int P = s.P;
@@ -777,8 +804,8 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st)
     const int j0 = q * NBS, jp = j0 - NBS, jq = j0 - 2 * NBS;
     const int nP = q < npan ? 1 : 0;
     const int nU = (q >= 1 && q < npan) ? (std::max(0, d - j0 - NBS) + NBS - 1) / NBS : 0;
-    const int nS = (q >= 1 && q - 1 < npan && jp > 0) ? (jp + NBS - 1) / NBS : 0;
-    const int nT = (q >= 2 && q - 2 < npan && jq > 0) ? (jq + NBS - 1) / NBS : 0;
+    const int nS = (with_t && q >= 1 && q - 1 < npan && jp > 0) ? (jp + NBS - 1) / NBS : 0;
+    const int nT = (with_t && q >= 2 && q - 2 < npan && jq > 0) ? (jq + NBS - 1) / NBS : 0;
     const int nx = nP + nU + nS + nT;
     if (nx == 0) continue;
     note_launch();
@@ -790,10 +817,55 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, cudaStream_t st)
   return e;
 }
 
+// Off-diagonal blocks of the compact-WY factor T of every combine of a stage, from its
+// diagonal blocks (width nb0, the combine's panels) and G = V_bot^T V_bot (the identity parts
+// of different reflectors do not overlap, so V^T V = V_bot^T V_bot off the diagonal):
+// T12 = -T11 G12 T22 for adjacent blocks of width w, w = nb0, 2 nb0, ..., a ragged last
+// block pairing with its full neighbour when their count is even.  Full pairs of a width
+// are one two-level batched GEMM (pairs x combines).
 template <typename T>
-Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot, cudaStream_t st) {
+Error assemble_t(const ckinv_ctx *ctx, const Stage<T> &s, int d, int nb0, cudaStream_t st) {
+  const int P = s.P, H = s.H;
+  const int64_t sM = (int64_t)H * d, sD = (int64_t)d * d;
+  T *G = nullptr, *W = nullptr;
+  CK_CUDA(cudaMallocAsync((void **)&G, sizeof(T) * (size_t)P * d * d, st));
+  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * (size_t)P * ((size_t)d * d / 4 + 1), st));
+  Error e = gemm_batched<T>(ctx, true, d, d, d, T(1), s.Vx + d, H, sM, s.Vx + d, H, sM, T(0), G, d, sD, P, st);
+  for (int w = nb0; w < d && !e.st; w *= 2) {
+    const int nfull = d / w, rem = d - nfull * w, np = nfull / 2;
+    const int64_t sp = 2LL * w * (d + 1);        // between pairs along the diagonal
+    if (np > 0) {
+      const int64_t sW = (int64_t)w * w, sW2 = (int64_t)np * w * w;
+      // W = G12 T22 ; T12 = -T11 W
+      if ((e = gemm_batched2<T>(ctx, false, w, w, w, T(1), G + (int64_t)w * d, d, sp, sD, s.Tm + w + (int64_t)w * d,
+                                d, sp, sD, T(0), W, w, sW, sW2, np, P, st)).st)
+        break;
+      if ((e = gemm_batched2<T>(ctx, false, w, w, w, T(-1), s.Tm, d, sp, sD, W, w, sW, sW2, T(0),
+                                s.Tm + (int64_t)w * d, d, sp, sD, np, P, st)).st)
+        break;
+    }
+    if ((nfull & 1) && rem > 0) {                // block nfull-1 (full) with the ragged block
+      const int c0 = (nfull - 1) * w;
+      const int64_t o12 = c0 + (int64_t)(c0 + w) * d, o22 = (c0 + w) + (int64_t)(c0 + w) * d;
+      const int64_t o11 = c0 + (int64_t)c0 * d;
+      if ((e = gemm_batched<T>(ctx, false, w, rem, rem, T(1), G + o12, d, sD, s.Tm + o22, d, sD, T(0), W, w,
+                               (int64_t)w * rem, P, st)).st)
+        break;
+      if ((e = gemm_batched<T>(ctx, false, w, rem, w, T(-1), s.Tm + o11, d, sD, W, w, (int64_t)w * rem, T(0),
+                               s.Tm + o12, d, sD, P, st)).st)
+        break;
+    }
+  }
+  cudaFreeAsync(G, st);
+  cudaFreeAsync(W, st);
+  return e;
+}
+
+template <typename T>
+Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot, cudaStream_t st,
+                   bool with_t = true) {
   if (s.stacked) {
-    CK_TRY(sq_factor<T>(ctx, s, d, st));
+    CK_TRY(sq_factor<T>(ctx, s, d, with_t, st));
     dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 64), s.P);
     note_launch();
     k_extract_r<T><<<g, 256, 0, st>>>(s.M, s.H, d, s.top, Rslot);
@@ -900,7 +972,30 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
         sd[l].stacked = true;
         note_launch();
         k_build_stack<double><<<g, 256, 0, st>>>(Rslot, sd[l].top, sd[l].bot, d, sd[l].M);
-        e = factor_stage<double>(ctx, sd[l], d, Rslot, st);
+        if ((e = factor_stage<double>(ctx, sd[l], d, Rslot, st, LEAF64)).st) break;
+        if (!LEAF64) {
+          // Q_hat is applied in FP32 after FP32 leaves: keep FP32 copies of the level's
+          // reflectors and T factors (the combine itself, and R, stay FP64)
+          Stage<float> &q = sf[l];
+          q.P = P;
+          q.H = 2 * d;
+          q.stacked = true;
+          q.top = sd[l].top;
+          q.bot = sd[l].bot;
+          const int64_t nv = (int64_t)P * 2 * d * d, nt = (int64_t)P * d * d;
+          if (cudaMallocAsync((void **)&q.Vx, sizeof(float) * nv, st) != cudaSuccess ||
+              cudaMallocAsync((void **)&q.Tm, sizeof(float) * nt, st) != cudaSuccess) {
+            e = fail(CKINV_ENOMEM, "tsqr FP32 reflector copies");
+            break;
+          }
+          owned.insert(owned.end(), {(void *)q.Vx, (void *)q.Tm});
+          note_launch();
+          k_narrow<<<(unsigned)std::min<int64_t>(ceil_div(nv, 256), 4096), 256, 0, st>>>(sd[l].Vx, q.Vx, nv);
+          note_launch();
+          k_narrow<<<(unsigned)std::min<int64_t>(ceil_div(nt, 256), 4096), 256, 0, st>>>(sd[l].Tm, q.Tm, nt);
+          // the FP64 combine formed T's diagonal blocks only; the rest in FP32 for Q_hat
+          if ((e = assemble_t<float>(ctx, q, d, sq_nb<double>(), st)).st) break;
+        }
       } else {
         if ((e = alloc_stage<float>(sf[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
         sf[l].stacked = true;
@@ -917,7 +1012,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     // ---- Q_hat, top-down
     const size_t qmax = std::max((size_t)L * Hl * d, (size_t)L * 2 * d * d);
     const size_t zmax = (size_t)L * d * d;
-    const size_t esz = (LEAF64 || nf64 > 0) ? sizeof(double) : sizeof(float);
+    const size_t esz = LEAF64 ? sizeof(double) : sizeof(float);
     void *Qs = nullptr, *Z1 = nullptr, *Z2 = nullptr;
     if (cudaMallocAsync(&Qs, esz * qmax, st) != cudaSuccess || cudaMallocAsync(&Z1, esz * zmax, st) != cudaSuccess ||
         cudaMallocAsync(&Z2, esz * zmax, st) != cudaSuccess) {
@@ -928,7 +1023,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     for (int l = Hn - 1; l >= 0 && !e.st; --l) {
       const int P = (int)levels[l].top.size();
       dim3 g((unsigned)std::min<int64_t>(ceil_div(2LL * d * d, 256), 256), P);
-      if (levels[l].fp64) {
+      if (LEAF64) {
         if ((e = apply_q<double>(ctx, sd[l], d, Xslot, (double *)Qs, (double *)Z1, (double *)Z2, st)).st) break;
         note_launch();
         k_scatter_x<double><<<g, 256, 0, st>>>((double *)Qs, sd[l].top, sd[l].bot, d, Xslot);
