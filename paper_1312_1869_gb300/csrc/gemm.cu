@@ -211,8 +211,10 @@ Error gemm_batched(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alp
     if (beta == T(1)) return ok();
     return fail(CKINV_EINVAL, "gemm_batched: K = 0 with beta != 1");
   }
-  // FP32 products big enough to fill 128 x 128 tensor-core tiles go to the tensor cores
-  if (sizeof(T) == 4 && ctx->gemm_tc && M >= 64 && N >= 64 && K >= 64 &&
+  // FP32 products big enough to fill 128 x 128 tensor-core tiles over at least four K blocks
+  // go to the tensor cores (with fewer, a tile's fixed costs - TMEM allocation, pipeline fill,
+  // the epilogue's read-modify-write - outweigh its MMAs)
+  if (sizeof(T) == 4 && ctx->gemm_tc && M >= 64 && N >= 64 && K >= 256 &&
       (double)M * N * (double)K * batch >= 3.0e7)
     return gemm_tc_f32(ctx, transA, M, N, K, (float)alpha, (const float *)A, lda, sA, (const float *)B, ldb, sB,
                        (float)beta, (float *)C, ldc, sC, batch, st);

@@ -141,6 +141,50 @@ __device__ __forceinline__ void split3(const float (&x)[8], uint32_t (&w)[kTerms
   }
 }
 
+// The three BF16 terms of four FP32 values, as packed BF16 pairs.
+__device__ __forceinline__ void split3_4(const float *x, uint32_t (&w)[kTerms][2]) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    float a = x[2 * u], b = x[2 * u + 1];
+#pragma unroll
+    for (int t = 0; t < kTerms; ++t) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+      w[t][u] = *reinterpret_cast<uint32_t *>(&h);
+      float2 back = __bfloat1622float2(h);
+      a -= back.x;
+      b -= back.y;
+    }
+  }
+}
+
+// Row (within a warp's 32) of lane l's quad t in the coalesced K-major layout: the four rows
+// of one step are r, r + 4, r + 1, r + 5, whose 128B-swizzled chunks fill both halves of the
+// shared-memory banks (rows r..r+3 would all land in the same half).
+__device__ __forceinline__ int kq_row(int t, int lane) {
+  return 8 * (t >> 1) + 2 * (t & 1) + 4 * ((lane >> 3) & 1) + (lane >> 4);
+}
+
+// A 32-row x 32-K block of a K-major operand (element (row, k) at P[k + row * ld]) read so
+// that each warp load touches four rows of 128 bytes: lane l takes K values k0 + 4 (l % 8)
+// .. +3 of rows rbase + kq_row(t, l), t < 8, into x[4 t .. 4 t + 3] (zero past K or the last
+// row).  Reading a whole row per lane instead made every load touch 32 lines and left the
+// kernel bound by L1 throughput.
+__device__ __forceinline__ void load_kmajor_c(const float *P, int64_t ld, int rbase, int rows, int k0, int K,
+                                              bool vec, int lane, float (&x)[32]) {
+  const int kk = k0 + 4 * (lane & 7);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int row = rbase + kq_row(t, lane);
+    if (row < rows && vec && kk + 4 <= K) {
+      const float4 v = *reinterpret_cast<const float4 *>(P + (int64_t)row * ld + kk);
+      x[4 * t] = v.x; x[4 * t + 1] = v.y; x[4 * t + 2] = v.z; x[4 * t + 3] = v.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[4 * t + u] = (row < rows && kk + u < K) ? P[(int64_t)row * ld + kk + u] : 0.f;
+    }
+  }
+}
+
 // 32 consecutive K values of row `row` of a K-major operand (element (row, k) at
 // P[k + row * ld]), zero past K or past the last row.
 __device__ __forceinline__ void load_kmajor(const float *P, int64_t ld, int row, int rows, int k0, int K, bool vec,
@@ -251,47 +295,59 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int h = pw >> 2;
     const uint32_t rowoff = (uint32_t)r * 128u;
     bool good = true;
+    // both operands of block kb + 1 are loaded while block kb is stored and the MMAs of the
+    // previous stage run, so neither load's latency sits between two stages
+    float xa[32], xb[32];
+    const int rb = (pw & 3) * 32;                  // this warp's 32 tile rows
+    auto load_block = [&](int kb) {
+      const int k0 = kb * GBK + h * 32;
+      if (TRANSA) load_kmajor_c(A, lda, m0 + rb, M, k0, K, vecA != 0, lane, xa);   // rows of op(A)
+      else load_mmajor(A, lda, m0 + r, M, k0, K, xa);
+      load_kmajor_c(B, ldb, n0 + rb, N, k0, K, vecB != 0, lane, xb);               // columns of B
+    };
+    // a whole row's 32 K values (M-major loads): four 16-byte chunks per term
+    auto store_row = [&](const float (&x)[32], uint32_t tile0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = x[8 * c + u];
+        uint32_t w[kTerms][4];
+        split3(v, w);
+        const uint32_t off = rowoff + ((((uint32_t)(h * 4 + c)) ^ ((uint32_t)r & 7u)) << 4);
+#pragma unroll
+        for (int t = 0; t < kTerms; ++t)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tile0 + t * kGTile + off), "r"(w[t][0]),
+                       "r"(w[t][1]), "r"(w[t][2]), "r"(w[t][3])
+                       : "memory");
+      }
+    };
+    // eight rows x 4 K values (coalesced K-major loads): half of a 16-byte chunk per term and row
+    auto store_quads = [&](const float (&x)[32], uint32_t tile0) {
+      const uint32_t chunk = (uint32_t)(h * 4 + ((lane & 7) >> 1)), half = (uint32_t)(lane & 1) * 8u;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const uint32_t row = (uint32_t)(rb + kq_row(t, lane));
+        uint32_t w[kTerms][2];
+        split3_4(&x[4 * t], w);
+        const uint32_t off = row * 128u + ((chunk ^ (row & 7u)) << 4) + half;
+#pragma unroll
+        for (int q = 0; q < kTerms; ++q)
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(tile0 + q * kGTile + off), "r"(w[q][0]), "r"(w[q][1])
+                       : "memory");
+      }
+    };
+    if (nkb > 0) load_block(0);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kGStages;
       const uint32_t ph = (uint32_t)(kb / kGStages) & 1u;
-      const int k0 = kb * GBK + h * 32;
-      float x[32];
-      // A block: rows m0 + r of op(A)
-      if (TRANSA) load_kmajor(A, lda, m0 + r, M, k0, K, vecA != 0, x);
-      else load_mmajor(A, lda, m0 + r, M, k0, K, x);
       if (!g_wait_lanes(empty(s), ph ^ 1u, abort_flag)) { good = false; break; }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = x[8 * c + u];
-        uint32_t w[kTerms][4];
-        split3(v, w);
-        const uint32_t off = rowoff + ((((uint32_t)(h * 4 + c)) ^ ((uint32_t)r & 7u)) << 4);
-#pragma unroll
-        for (int t = 0; t < kTerms; ++t)
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a_tile(s, t) + off), "r"(w[t][0]),
-                       "r"(w[t][1]), "r"(w[t][2]), "r"(w[t][3])
-                       : "memory");
-      }
-      // B block: rows n0 + r of B^T (column n0 + r of B, K contiguous)
-      load_kmajor(B, ldb, n0 + r, N, k0, K, vecB != 0, x);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = x[8 * c + u];
-        uint32_t w[kTerms][4];
-        split3(v, w);
-        const uint32_t off = rowoff + ((((uint32_t)(h * 4 + c)) ^ ((uint32_t)r & 7u)) << 4);
-#pragma unroll
-        for (int t = 0; t < kTerms; ++t)
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(b_tile(s, t) + off), "r"(w[t][0]),
-                       "r"(w[t][1]), "r"(w[t][2]), "r"(w[t][3])
-                       : "memory");
-      }
+      if (TRANSA) store_quads(xa, a_tile(s, 0));
+      else store_row(xa, a_tile(s, 0));
+      store_quads(xb, b_tile(s, 0));
       g_fence_async();
       g_mbar_arrive(full(s));
+      if (kb + 1 < nkb) load_block(kb + 1);
     }
     // epilogue: TMEM lane quadrant warp % 4, columns split between the two warps of a quadrant
     if (good && nkb > 0 && g_wait_lanes(accum_bar, 0u, abort_flag)) {
