@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
 #pragma unroll
     for (int b = 0; b < 4; ++b) { acc[a][b] = 0.f; accd[a][b] = 0.0; }
   __syncthreads();
-  int step = 0;
-  for (int64_t k0 = rb; k0 < re; k0 += 32) {
+  // the next 32 rows are fetched into registers while the current ones are multiplied
+  float lr[TM / 8], mr[TN / 8];
+  auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int q = 0; q < TM / 8; ++q) {
       int e = tid + 256 * q;
@@ -55,16 +56,31 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
           lv = L[k + (int64_t)(i0 + c) * ldl];
         }
       }
-      Ls[kk][c] = lv;
+      lr[q] = lv;
     }
 #pragma unroll
     for (int q = 0; q < TN / 8; ++q) {
       int e = tid + 256 * q;
       int kk = e % 32, c = e / 32;
       int64_t k = k0 + kk;
-      Ms[kk][c] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
+      mr[q] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
+    }
+  };
+  if (rb < re) fetch(rb);
+  int step = 0;
+  for (int64_t k0 = rb; k0 < re; k0 += 32) {
+#pragma unroll
+    for (int q = 0; q < TM / 8; ++q) {
+      int e = tid + 256 * q;
+      Ls[e % 32][e / 32] = lr[q];
+    }
+#pragma unroll
+    for (int q = 0; q < TN / 8; ++q) {
+      int e = tid + 256 * q;
+      Ms[e % 32][e / 32] = mr[q];
     }
     __syncthreads();
+    if (k0 + 32 < re) fetch(k0 + 32);
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
       float a[4], b[4];
@@ -121,19 +137,39 @@ __global__ void __launch_bounds__(256) k_tsprod_dd(int64_t n, int d1, int d2, co
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) { hs[a][b] = 0.f; lc[a][b] = 0.f; acc[a][b] = 0.0; }
+  // the next 32 rows are fetched into registers while the current ones are multiplied
+  float lr[8], mr[4];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int e = tid + 256 * q;
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      lr[q] = (k < re && i0 + c < d1) ? L[k + (int64_t)(i0 + c) * ldl] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int kk = e % 32, c = e / 32;
+      int64_t k = k0 + kk;
+      mr[q] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
+    }
+  };
+  if (rb < re) fetch(rb);
   int step = 0;
   for (int64_t k0 = rb; k0 < re; k0 += 32) {
-    for (int e = tid; e < 32 * 64; e += 256) {
-      int kk = e % 32, c = e / 32;
-      int64_t k = k0 + kk;
-      Ls[kk][c] = (k < re && i0 + c < d1) ? L[k + (int64_t)(i0 + c) * ldl] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int e = tid + 256 * q;
+      Ls[e % 32][e / 32] = lr[q];
     }
-    for (int e = tid; e < 32 * 32; e += 256) {
-      int kk = e % 32, c = e / 32;
-      int64_t k = k0 + kk;
-      Ms[kk][c] = (k < re && j0 + c < d2) ? M[k + (int64_t)(j0 + c) * ldm] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      Ms[e % 32][e / 32] = mr[q];
     }
     __syncthreads();
+    if (k0 + 32 < re) fetch(k0 + 32);
 #pragma unroll 4
     for (int kk = 0; kk < 32; ++kk) {
       float b0 = Ms[kk][tx * 2], b1 = Ms[kk][tx * 2 + 1];
@@ -197,22 +233,29 @@ __global__ void __launch_bounds__(256) k_residual_dd(int64_t n, int d, int m, co
     }
     __syncthreads();
     if (i < n) {
-      int kmax = min(64, d - k0);
-      for (int kk = 0; kk < kmax; ++kk) {
-        float q = Q[i + (int64_t)(k0 + kk) * ldq];
+      const int kmax = min(64, d - k0);
+      for (int kb = 0; kb < kmax; kb += 16) {     // sixteen loads of Q in flight per thread
+        float qv[16];
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const float4 h4 = *reinterpret_cast<const float4 *>(&Sh[kk][4 * c4]);
-          const float4 l4 = *reinterpret_cast<const float4 *>(&Sl[kk][4 * c4]);
-          const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+        for (int u = 0; u < 16; ++u) qv[u] = (kb + u < kmax) ? Q[i + (int64_t)(k0 + kb + u) * ldq] : 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int c = 4 * c4 + u;
-            float p = q * hv[u], e = fmaf(q, hv[u], -p);
-            float sum, r;
-            two_sum(hs[c], p, sum, r);
-            hs[c] = sum;
-            lc[c] += r + fmaf(q, lv[u], e);
+        for (int t = 0; t < 16; ++t) {
+          const float q = qv[t];
+          const int kk = kb + t;
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const float4 h4 = *reinterpret_cast<const float4 *>(&Sh[kk][4 * c4]);
+            const float4 l4 = *reinterpret_cast<const float4 *>(&Sl[kk][4 * c4]);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int c = 4 * c4 + u;
+              float p = q * hv[u], e = fmaf(q, hv[u], -p);
+              float sum, r;
+              two_sum(hs[c], p, sum, r);
+              hs[c] = sum;
+              lc[c] += r + fmaf(q, lv[u], e);
+            }
           }
         }
       }
@@ -593,16 +636,21 @@ __global__ void __launch_bounds__(256) k_apply_x(int64_t n, int d, int m, const 
     }
     __syncthreads();
     if (i < n) {
-      int kmax = min(64, d - k0);
-      for (int kk = 0; kk < kmax; ++kk) {
-        float q = Q[i + (int64_t)(k0 + kk) * ldq];
+      const int kmax = min(64, d - k0);
+      for (int kb = 0; kb < kmax; kb += 16) {     // sixteen loads of Q in flight per thread
+        float q[16];
 #pragma unroll
-        for (int c4 = 0; c4 < 8; ++c4) {
-          const float4 v = *reinterpret_cast<const float4 *>(&Vs[kk][4 * c4]);
-          acc[4 * c4 + 0] = fmaf(q, v.x, acc[4 * c4 + 0]);
-          acc[4 * c4 + 1] = fmaf(q, v.y, acc[4 * c4 + 1]);
-          acc[4 * c4 + 2] = fmaf(q, v.z, acc[4 * c4 + 2]);
-          acc[4 * c4 + 3] = fmaf(q, v.w, acc[4 * c4 + 3]);
+        for (int u = 0; u < 16; ++u) q[u] = (kb + u < kmax) ? Q[i + (int64_t)(k0 + kb + u) * ldq] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 v = *reinterpret_cast<const float4 *>(&Vs[kb + u][4 * c4]);
+            acc[4 * c4 + 0] = fmaf(q[u], v.x, acc[4 * c4 + 0]);
+            acc[4 * c4 + 1] = fmaf(q[u], v.y, acc[4 * c4 + 1]);
+            acc[4 * c4 + 2] = fmaf(q[u], v.z, acc[4 * c4 + 2]);
+            acc[4 * c4 + 3] = fmaf(q[u], v.w, acc[4 * c4 + 3]);
+          }
         }
       }
     }
