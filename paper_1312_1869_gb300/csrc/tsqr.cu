@@ -37,21 +37,32 @@ int panel_threads(int h) {
   return h > 1024 ? 512 : (h > 256 ? 256 : 128);
 }
 
-// Reduce NV per-thread values over the whole CTA; result in out[0..NV).
+// Reduce NV per-thread values over the whole CTA; result in out[0..NV).  Within a warp the
+// NV values are reduced by recursive halving (NV - 1 + 32 / NV shuffles instead of 5 NV):
+// at offset o every lane keeps half of its values, adds its partner's copy of that half, and
+// after the halvings lane l holds the warp sum of value kept(l) (lanes that share a value
+// finish with plain butterflies).
 template <typename T, int NV, int NT>
 __device__ __forceinline__ void block_sum(T (&vals)[NV], T *red, T *out) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int idx = 0;                                   // index of the value this lane ends with
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    T x = vals[v];
+  for (int o = 16, n = NV; n > 1; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;             // keep the upper half of the n values
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    vals[v] = x;
+    for (int j = 0; j < n / 2; ++j) {
+      const T send = up ? vals[j] : vals[j + n / 2];
+      const T keep = up ? vals[j + n / 2] : vals[j];
+      vals[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    idx = 2 * idx + (up ? 1 : 0);
   }
-  if (lane == 0) {
+  constexpr int kFirst = 32 / NV;                // lanes still sharing one value
+  T x = vals[0];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) red[warp * NV + v] = vals[v];
-  }
+  for (int o = kFirst / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((lane & (kFirst - 1)) == 0) red[warp * NV + idx] = x;
   __syncthreads();
   if (threadIdx.x < NV) {
     T s = 0;
@@ -125,33 +136,31 @@ __global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, 
 
   for (int jj = 0; jj < NB; ++jj) {
     T *x = Ps + jj * hp;
-    T part[1] = {0};
-    for (int r = jj + 1 + tid; r < h; r += PT) part[0] += x[r] * x[r];
-    block_sum<T, 1, PT>(part, red, sums);
-    // every thread derives the reflector from the reduced norm (no broadcast round trip)
-    const T alpha = x[jj];
-    const T sig = sums[0];
-    const T normx = sqrt(alpha * alpha + sig);
-    T tau = 0, rd = 0, inv_head = 0;
-    if (normx > 0) {
-      const T s = alpha >= 0 ? T(1) : T(-1);
-      const T head = alpha + s * normx;
-      inv_head = T(1) / head;
-      tau = T(2) / (T(1) + sig * inv_head * inv_head);
-      rd = -s * normx;
-    }
-    // v = x / head on this thread's rows, then its dots with the other panel columns
+    // one pass and one reduction per step: raw dots of x (rows below jj) with every panel
+    // column, c == jj giving |x|^2; the reflector v = x / head is applied through them
     T dots[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) dots[c] = 0;
     for (int r = jj + 1 + tid; r < h; r += PT) {
-      T vr = x[r] * inv_head;
-      x[r] = vr;
+      const T xr = x[r];
 #pragma unroll
-      for (int c = 0; c < NB; ++c) dots[c] += (c == jj) ? T(0) : Ps[c * hp + r] * vr;
+      for (int c = 0; c < NB; ++c) dots[c] += Ps[c * hp + r] * xr;
     }
     block_sum<T, NB, PT>(dots, red, sums);
-    if (tid < NB && tid != jj) wv[tid] = Ps[tid * hp + jj] + sums[tid];
+    // every thread derives the reflector from the reduced norm (no broadcast round trip)
+    const T alpha = x[jj];
+    const T sig = sums[jj];
+    const T normx = sqrt(alpha * alpha + sig);
+    T tau = 0, rd = 0, inv_head = 0;
+    if (normx > 0) {
+      const T sg = alpha >= 0 ? T(1) : T(-1);
+      const T head = alpha + sg * normx;
+      inv_head = T(1) / head;
+      tau = T(2) / (T(1) + sig * inv_head * inv_head);
+      rd = -sg * normx;
+    }
+    for (int r = jj + 1 + tid; r < h; r += PT) x[r] *= inv_head;   // this thread's rows only
+    if (tid < NB && tid != jj) wv[tid] = Ps[tid * hp + jj] + sums[tid] * inv_head;
     __syncthreads();
     if (tid == 0) x[jj] = rd;
     for (int c = jj + 1; c < NB; ++c) {
