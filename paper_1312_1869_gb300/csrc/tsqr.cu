@@ -503,10 +503,10 @@ __device__ void sq_panel_role(T *sm, T *M, T *Vx, T *Tm, int d, int j0) {
       Vx[d + i + (int64_t)(j0 + c) * H] = (i <= j0 + c) ? Vp[c * d + i] * Ih[c] : T(0);
 }
 
-// Panel jp's block reflector applied to NBS columns from cb (V_panel and C_bot use
-// bottom rows 0..jp+nb-1).
+// Panel jp's block reflector applied to nt tiles of NBS columns from cb0 (V_panel and C_bot
+// use bottom rows 0..jp+nb-1); V_panel and T_kk are staged once for all of them.
 template <typename T>
-__device__ void sq_update_role(T *sm, T *M, const T *Vx, const T *Tm, int d, int jp, int cb) {
+__device__ void sq_update_role(T *sm, T *M, const T *Vx, const T *Tm, int d, int jp, int cb0, int nt) {
   constexpr int NBS = sq_nb<T>(), LD = NBS + 1;
   T *Vs = sm;                                     // rows x NBS: the panel's V_bot
   T *Cs = Vs + (size_t)d * LD;                    // rows x NBS: C_bot tile
@@ -516,42 +516,50 @@ __device__ void sq_update_role(T *sm, T *M, const T *Vx, const T *Tm, int d, int
   T *W2 = W + NBS * LD;
   const int H = 2 * d;
   const int nb = min(NBS, d - jp), rows = jp + nb;
-  const int nc = min(NBS, d - cb);
   const int tid = threadIdx.x;
   stage_tile<T, 8>(Vs, LD, 1, Vx + d + (int64_t)jp * H, H, rows, NBS, nb);
-  stage_tile<T, 8>(Cs, LD, 1, M + d + (int64_t)cb * H, H, rows, NBS, nc);
   for (int e = tid; e < NBS * NBS; e += blockDim.x) {
     const int r = e % NBS, cc = e / NBS;
-    Ctp[r * LD + cc] = (r < nb && cc < nc) ? M[jp + r + (int64_t)(cb + cc) * H] : T(0);
     Tk[r * LD + cc] = (r < nb && cc < nb) ? Tm[(jp + r) + (int64_t)(jp + cc) * d] : T(0);
   }
-  __syncthreads();
-  // W = C_top + V^T C_bot
-  constexpr int KS = sq_split(NBS * NBS);
-  for (int e = tid; e < NBS * NBS * KS; e += blockDim.x) {
-    const int o = e / KS, part = e % KS;
-    const int cc = o % NBS, r = o / NBS;
-    const T acc = group_dot<T, KS>(rows, part, [&](int i) { return Vs[i * LD + r] * Cs[i * LD + cc]; });
-    if (part == 0) W[r * LD + cc] = Ctp[r * LD + cc] + acc;
-  }
-  __syncthreads();
-  // W2 = T_kk^T W ; C_top -= W2
-  for (int e = tid; e < NBS * NBS; e += blockDim.x) {
-    const int cc = e % NBS, r = e / NBS;
-    T acc = 0;
-    for (int k = 0; k <= r; ++k) acc += Tk[k * LD + r] * W[k * LD + cc];
-    W2[r * LD + cc] = acc;
-    if (r < nb && cc < nc) M[jp + r + (int64_t)(cb + cc) * H] = Ctp[r * LD + cc] - acc;
-  }
-  __syncthreads();
-  // C_bot -= V W2
-  for (int e = tid; e < rows * NBS; e += blockDim.x) {
-    const int cc = e % NBS, i = e / NBS;
-    if (cc >= nc) continue;
-    T acc = 0;
+  for (int t = 0; t < nt; ++t) {
+    const int cb = cb0 + t * NBS;
+    if (cb >= d) break;
+    const int nc = min(NBS, d - cb);
+    if (t > 0) __syncthreads();                   // the previous tile's reads of Cs, W2 are done
+    stage_tile<T, 8>(Cs, LD, 1, M + d + (int64_t)cb * H, H, rows, NBS, nc);
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int r = e % NBS, cc = e / NBS;
+      Ctp[r * LD + cc] = (r < nb && cc < nc) ? M[jp + r + (int64_t)(cb + cc) * H] : T(0);
+    }
+    __syncthreads();
+    // W = C_top + V^T C_bot
+    constexpr int KS = sq_split(NBS * NBS);
+    for (int e = tid; e < NBS * NBS * KS; e += blockDim.x) {
+      const int o = e / KS, part = e % KS;
+      const int cc = o % NBS, r = o / NBS;
+      const T acc = group_dot<T, KS>(rows, part, [&](int i) { return Vs[i * LD + r] * Cs[i * LD + cc]; });
+      if (part == 0) W[r * LD + cc] = Ctp[r * LD + cc] + acc;
+    }
+    __syncthreads();
+    // W2 = T_kk^T W ; C_top -= W2
+    for (int e = tid; e < NBS * NBS; e += blockDim.x) {
+      const int cc = e % NBS, r = e / NBS;
+      T acc = 0;
+      for (int k = 0; k <= r; ++k) acc += Tk[k * LD + r] * W[k * LD + cc];
+      W2[r * LD + cc] = acc;
+      if (r < nb && cc < nc) M[jp + r + (int64_t)(cb + cc) * H] = Ctp[r * LD + cc] - acc;
+    }
+    __syncthreads();
+    // C_bot -= V W2
+    for (int e = tid; e < rows * NBS; e += blockDim.x) {
+      const int cc = e % NBS, i = e / NBS;
+      if (cc >= nc) continue;
+      T acc = 0;
 #pragma unroll 8
-    for (int r = 0; r < NBS; ++r) acc += Vs[i * LD + r] * W2[r * LD + cc];
-    M[d + i + (int64_t)(cb + cc) * H] = Cs[i * LD + cc] - acc;
+      for (int r = 0; r < NBS; ++r) acc += Vs[i * LD + r] * W2[r * LD + cc];
+      M[d + i + (int64_t)(cb + cc) * H] = Cs[i * LD + cc] - acc;
+    }
   }
 }
 
@@ -632,7 +640,7 @@ __device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) 
 // (into buffer (q-1) & 1), the rest form T's blocks for panel q-2 (from buffer q & 1).
 template <typename T>
 __global__ void __launch_bounds__(SQ_THREADS, sizeof(T) == 8 ? 3 : 1) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
-                                                        int nS) {
+                                                        int nS, int uw) {
   constexpr int NBS = sq_nb<T>();
   extern __shared__ __align__(16) uint8_t sm_raw[];
   T *sm = reinterpret_cast<T *>(sm_raw);
@@ -650,7 +658,7 @@ __global__ void __launch_bounds__(SQ_THREADS, sizeof(T) == 8 ? 3 : 1) k_sq_step(
   }
   b -= nP;
   if (b < nU) {
-    sq_update_role<T>(sm, M, Vx, Tm, d, j0 - NBS, j0 + NBS + b * NBS);
+    sq_update_role<T>(sm, M, Vx, Tm, d, j0 - NBS, j0 + NBS + b * uw * NBS, uw);
     return;
   }
   b -= nU;
@@ -808,17 +816,23 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, bool with_t, cud
   CK_CUDA(cudaFuncSetAttribute(k_sq_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   T *S = nullptr;
   CK_CUDA(cudaMallocAsync((void **)&S, sizeof(T) * 2 * (size_t)P * d * NBS, st));
+  // update tiles per CTA: with many combines the level is FP64-throughput bound, and a CTA
+  // that stages the panel's reflectors once for several tiles wastes less; with few it is
+  // latency bound, and one tile per CTA keeps each CTA short
+  const int uw = (sizeof(T) == 8 && P >= 16) ? 4 : 1;
   Error e = ok();
   for (int q = 0; q <= npan + 1 && !e.st; ++q) {
     const int j0 = q * NBS, jp = j0 - NBS, jq = j0 - 2 * NBS;
     const int nP = q < npan ? 1 : 0;
-    const int nU = (q >= 1 && q < npan) ? (std::max(0, d - j0 - NBS) + NBS - 1) / NBS : 0;
+    const int ntile = (q >= 1 && q < npan) ? (std::max(0, d - j0 - NBS) + NBS - 1) / NBS : 0;
+    const int nU = (ntile + uw - 1) / uw;
     const int nS = (with_t && q >= 1 && q - 1 < npan && jp > 0) ? (jp + NBS - 1) / NBS : 0;
     const int nT = (with_t && q >= 2 && q - 2 < npan && jq > 0) ? (jq + NBS - 1) / NBS : 0;
     const int nx = nP + nU + nS + nT;
     if (nx == 0) continue;
     note_launch();
-    k_sq_step<T><<<dim3((unsigned)nx, (unsigned)P), SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, S, d, q, nP, nU, nS);
+    k_sq_step<T><<<dim3((unsigned)nx, (unsigned)P), SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, S, d, q, nP, nU, nS,
+                                                                             uw);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
   }
