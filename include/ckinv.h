@@ -24,7 +24,7 @@
  *     one-line description of the last failure on that context.
  *   - A context is not thread-safe: use one per host thread.
  *
- * Definitions used throughout (the paper writes no nugget; see DESIGN notes):
+ * Definitions used throughout (the paper writes no nugget; tau enters only the solve):
  *   K0 = variance * rho(x_i, x_k)      noise-free kernel matrix,  rho(0) = 1
  *   Omega[k, j] = c r_k (-1)^popcount(k & p_j),  c = N^-1/2, N = 2^ceil(log2 n)
  *   Y = K0 Omega = Q_hat R  (diag(R) >= 0),  B = Omega^T Q_hat,  C' = R^T + tau B
@@ -82,7 +82,8 @@ typedef struct {
   int32_t prec;            /* ckinv_precision of the sketch contraction */
   uint64_t seed;           /* seed of the counter-based generator drawing R and P */
   int32_t refine_steps;    /* FP64 iterative-refinement steps of the final solve (0..4) */
-  int32_t tree_fp64_levels;/* top levels of the R tree combined in FP64; -1 = all */
+  int32_t tree_fp64_levels;/* top levels of the R tree combined in FP64; -1 = all.  Q_hat
+                              is formed in the leaves' precision either way */
   int32_t leaf_fp64;       /* 1: per-block Householder (and so the whole tree) in FP64 */
   int32_t reserved;        /* must be 0 */
 } ckinv_plan_desc;
