@@ -3,11 +3,13 @@
 // The TSQR is a sequence of stages, each a batch of independent dense QRs of the same
 // shape H x d: the leaves (blocks of b rows of Y, Eq. 1) and then, level by level, the
 // combines of stacked pairs of R factors [R_a; R_b] (2d x d, Eqs. 2-3).  Pairs are formed
-// left to right at every level and an odd last node passes up unchanged.  Each dense QR is
+// left to right at every level and an odd last node passes up unchanged.  A leaf QR is
 // Householder QR in recursive blocked form (Elmroth & Gustavson): column ranges are split
 // in two down to 16-column panels, which one CTA per problem factors in shared memory with
 // warp-shuffle reductions; everything else - applying the left part's reflectors to the
 // right part and assembling the compact-WY factor T (Q = I - V T V^T) - is batched GEMM.
+// A combine exploits the stacked-triangle structure and runs panel by panel, one launch per
+// panel for all combines of a level (k_sq_step, below).
 // Leaves run in FP32 (or FP64 on request), the top `fp64_levels` tree levels in FP64; the
 // R factors passed between levels are FP64 throughout.  Q_hat is formed top-down from the
 // root's coefficient block D = sign(diag R): each stage maps its blocks X to
