@@ -129,6 +129,21 @@ def sampled_sketch_error(ck, Y, pts, cfg, seed, rows):
     return float(np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo))
 
 
+def job_rate(local_ms, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of `steps` steps on each of `world` ranks: the slowest rank's
+    time (max over ranks, behind a barrier) sets it.  Returns (units per second, ms per step
+    of the slowest rank).  `dist` is torch.distributed (None for one process); `device` is
+    where the reduction tensor lives (the rank's GPU under NCCL, "cpu" under gloo)."""
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return world * steps / (total_ms / 1e3), total_ms / steps
+
+
 def oracle_sample_time(cfg, rows_sample, seed):
     """FP64 CPU oracle on a bounded sample: Omega (built once per solve) and the sketch rows
     [0, rows_sample) of the workload.  Returns (seconds, extrapolated seconds per solve:
@@ -292,15 +307,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = (ck.kernel_launches() - launches0) // max(1, args.steps)
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    value, ms_step = job_rate(float(np.sum(step_ms)), args.steps, world, dist, dev)
     ck.check(ctx)
-    value = world * args.steps / (total_ms / 1e3)
-    ms_step = total_ms / args.steps
 
     # accuracy of the sketch on sampled rows (a fresh sketch: TSQR overwrites Y)
     y_err = None
@@ -322,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
         plan.seed = 777 + i
         ck.kinv_a(ctx, plan, kern, pts_h, A_h, X_h)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value, _ = job_rate(1e3 * (time.perf_counter() - t0), e2e_steps, world, dist, dev)
     h2d = pts_np.nbytes + A_np.nbytes
     d2h = X_h.numel() * 4
 
@@ -384,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
                            "l2": "flushed between steps (256 MB write); Y and Q_hat (537 MB each) exceed L2"},
                 "tflops": achieved, "sketch_ms": sk_s * 1e3, "sketch_rel_err_sampled": y_err,
                 "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "clocks": clk}
         if forms is not None:
