@@ -24,5 +24,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   tsqr          pinned by equality with the direct QR's R
   lowrank       pinned by dense Cholesky/LU solves of tau I + K_N, exact-rank recovery,
                 and central finite differences of the NLL
+  transforms    (Hartley and cosine forms of Omega, for the structured fast sketch that
+                comes next) pinned by numpy's FFT, scipy's orthonormal DCT-II and
+                Omega^T Omega = I at orders that are not powers of two
+  projection    (column-space error, predictive mean) pinned by the dense definition,
+                exact recovery for rank(K0) <= d, and the textbook GP mean by Cholesky
   theory bounds (Theorems 3-4): parity unpinned, constants are not stated in the paper
 """

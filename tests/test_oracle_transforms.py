@@ -1,0 +1,120 @@
+"""Pins of the oracle's Hartley and cosine forms of Omega (Definition 1, Sec. 3.2) and of the
+column-space error and predictive mean (Sec. 3.1, Sec. 4, Sec. 5), all on CPU.
+
+Each pin is something other than the oracle itself: a library transform (numpy FFT, scipy
+DCT), an identity the definition forces (orthonormal columns for every n), or a result the
+mathematics fixes (exact recovery when rank(K0) <= d; the exact GP mean when K_tilde = K).
+"""
+import numpy as np
+import pytest
+
+from oracle import kernels as okk
+from oracle import omega as oom
+from oracle import projection as opr
+from oracle import transforms as otr
+from oracle import householder as ohh
+
+
+@pytest.mark.parametrize("n", [7, 64, 1000])
+def test_hartley_matrix_is_the_fft_combination(n):
+    """sum_k x_k cas(2 pi k p / n) = Re(FFT x)_p - Im(FFT x)_p (numpy's FFT uses e^{-i...})."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n)
+    k = np.arange(n)
+    T = otr.hartley_entries(k[:, None], k[None, :], n)
+    F = np.fft.fft(x)
+    assert np.allclose(T.T @ x, F.real - F.imag, atol=1e-10 * np.abs(x).sum())
+
+
+@pytest.mark.parametrize("n", [5, 64, 1000])
+def test_cosine_matrix_is_the_orthonormal_dct2(n):
+    scipy_fft = pytest.importorskip("scipy.fft")
+    rng = np.random.default_rng(n + 1)
+    x = rng.standard_normal(n)
+    k = np.arange(n)
+    T = otr.cosine_entries(k[:, None], k[None, :], n)
+    assert np.allclose(T.T @ x, scipy_fft.dct(x, type=2, norm="ortho"), atol=1e-12 * np.abs(x).sum())
+
+
+@pytest.mark.parametrize("transform", ["hartley", "cosine"])
+@pytest.mark.parametrize("n,d", [(1000, 48), (777, 272), (64, 64)])
+def test_structured_omega_has_orthonormal_columns_for_any_n(transform, n, d):
+    """Definition 1 asks for orthonormal columns; these transforms give them without padding."""
+    O = otr.omega_matrix_t(n, d, 5, transform)
+    assert O.shape == (n, d)
+    assert np.abs(O.T @ O - np.eye(d)).max() <= 1e-12
+
+
+def test_subsample_is_a_uniform_subset_of_the_transform_order():
+    n, d = 1000, 100
+    hits = np.zeros(n)
+    for s in range(200):
+        c = otr.subsample_columns_n(n, d, s)
+        assert len(np.unique(c)) == d and c.min() >= 0 and c.max() < n and np.all(np.diff(c) > 0)
+        hits[c] += 1
+    expected = 200 * d / n
+    chi2 = float(np.sum((hits - expected) ** 2 / expected))
+    assert chi2 < n + 5 * np.sqrt(2 * n)             # about 1 +- 0.22 per degree of freedom
+
+
+def _exact_rank_points_kernel(n, r, seed):
+    """K0 = E D E^T with E an orthonormalised Gaussian n x r and exponentially decaying D
+    (the construction of the blocking simulation, Sec. 5)."""
+    rng = np.random.default_rng(seed)
+    E, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    D = np.exp(-0.01 * np.arange(r))
+    return (E * D) @ E.T
+
+
+@pytest.mark.parametrize("transform", ["wht", "hartley", "cosine"])
+def test_exact_recovery_of_the_column_space(transform):
+    """rank(K0) = r <= d: the sketch's Q spans K0's column space, so ||K - QQ^T K|| = 0."""
+    n, r, d = 512, 20, 32
+    K = _exact_rank_points_kernel(n, r, 3)
+    O = oom.omega_matrix(n, d, 1) if transform == "wht" else otr.omega_matrix_t(n, d, 1, transform)
+    Q, _ = ohh.qr(K @ O)
+    err = np.linalg.norm(K - Q @ (Q.T @ K)) / np.linalg.norm(K)
+    assert err <= 1e-12
+
+
+def test_colspace_error_matches_its_definition_and_decreases_with_d():
+    n = 400
+    pts = np.random.default_rng(0).random((n, 2))
+    K = okk.kernel_matrix(pts, pts, okk.SE, 0.2, 1.0)
+    errs = []
+    for d in (8, 16, 32, 64):
+        Q, _ = ohh.qr(K @ oom.omega_matrix(n, d, 2))
+        e = opr.colspace_error(pts, okk.SE, 0.2, 1.0, Q, col_block=64)
+        dense = np.linalg.norm(K - Q @ Q.T @ K) / np.linalg.norm(K)
+        assert abs(e - dense) <= 1e-12 * max(dense, 1e-300) + 1e-15
+        errs.append(e)
+    assert all(a > b for a, b in zip(errs, errs[1:]))    # more columns, smaller error
+
+
+def test_predictive_mean_is_exact_when_the_kernel_has_rank_at_most_d():
+    """With a kernel whose K0 has rank <= d the method's K_tilde is K0 + tau I exactly, so
+    mu* = K0(X*, X) (K0 + tau I)^-1 y (the textbook GP mean, by Cholesky)."""
+    n, m_new, d, tau = 256, 17, 64, 1e-3
+    rng = np.random.default_rng(4)
+    pts = rng.random((n, 1)) * 0.02                  # points this close: K0 numerically rank-1-ish
+    new = rng.random((m_new, 1)) * 0.02
+    ell = 50.0                                        # SE with a huge lengthscale: rank(K0) <= d in FP64
+    y = rng.standard_normal(n)
+    mu = opr.predictive_mean(pts, y, new, okk.SE, ell, 1.0, tau, d, 0, 128)
+    K = okk.kernel_matrix(pts, pts, okk.SE, ell, 1.0) + tau * np.eye(n)
+    L = np.linalg.cholesky(K)
+    alpha = np.linalg.solve(L.T, np.linalg.solve(L, y))
+    mu_exact = okk.kernel_matrix(new, pts, okk.SE, ell, 1.0) @ alpha
+    assert np.allclose(mu, mu_exact, rtol=1e-6, atol=1e-6 * np.abs(mu_exact).max())
+
+
+def test_a_planted_sign_error_in_the_hartley_kernel_is_caught():
+    """cos - sin instead of cos + sin (a plausible slip) breaks the FFT pin."""
+    n = 64
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(n)
+    k = np.arange(n)
+    a = 2.0 * np.pi * ((k[:, None] * k[None, :]) % n) / n
+    wrong = np.cos(a) - np.sin(a)
+    F = np.fft.fft(x)
+    assert not np.allclose(wrong.T @ x, F.real - F.imag, atol=1e-8)
