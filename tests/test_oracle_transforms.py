@@ -118,3 +118,20 @@ def test_a_planted_sign_error_in_the_hartley_kernel_is_caught():
     wrong = np.cos(a) - np.sin(a)
     F = np.fft.fft(x)
     assert not np.allclose(wrong.T @ x, F.real - F.imag, atol=1e-8)
+
+
+@pytest.mark.parametrize("A,B", [(4, 8), (16, 2), (1, 32)])
+def test_kronecker_split_of_the_walsh_hadamard_product(A, B):
+    """H_N = H_A (x) H_B in Sylvester order, so (H_N v)[p_a B + p_b] =
+    sum_{k_a} H_A[k_a, p_a] (H_B v_{k_a})[p_b]: the identity a structured fast sketch uses to
+    replace the dense Omega by B-point transforms and a signed gather."""
+    N = A * B
+    rng = np.random.default_rng(A * 100 + B)
+    v = rng.standard_normal(N)
+    k = np.arange(N)
+    dense = oom.hadamard_entries(k[:, None], k[None, :]) @ v
+    HB = oom.hadamard_entries(np.arange(B)[:, None], np.arange(B)[None, :])
+    HA = oom.hadamard_entries(np.arange(A)[:, None], np.arange(A)[None, :])
+    U = v.reshape(A, B) @ HB.T                         # row k_a: the B-point transform of block k_a
+    split = (HA.T @ U).reshape(N)                      # output p = p_a * B + p_b
+    assert np.allclose(split, dense, atol=1e-12 * np.abs(v).sum())
