@@ -106,3 +106,43 @@ def test_dropped_half_in_gradient_is_caught(monkeypatch):
     _, g = F(math.log(0.25))
     fd = (F(math.log(0.25) + h)[0] - F(math.log(0.25) - h)[0]) / (2 * h)
     assert abs(g[0] - fd) > 1e-3 * abs(fd)
+
+
+# ------------------------------------------------------------------ transforms, projection
+def test_wrong_cosine_normalisation_is_caught(monkeypatch):
+    """s_0 = (2/n)^(1/2) like the other columns (a plausible slip) breaks orthonormality."""
+    from oracle import transforms as tr
+
+    def bad(k, p, n):
+        k = np.asarray(k, dtype=np.int64)
+        p = np.asarray(p, dtype=np.int64)
+        return np.sqrt(2.0 / n) * np.cos(np.pi * (((2 * k + 1) * p) % (4 * n)) / (2.0 * n))
+
+    monkeypatch.setattr(tr, "cosine_entries", bad)
+    n = 500
+    x = np.random.default_rng(0).standard_normal(n)
+    k = np.arange(n)
+    scipy_fft = pytest.importorskip("scipy.fft")
+    assert not np.allclose(bad(k[:, None], k[None, :], n).T @ x, scipy_fft.dct(x, type=2, norm="ortho"))
+
+
+def test_wrong_hartley_scale_is_caught(monkeypatch):
+    """c = 1/n instead of n^(-1/2) breaks the orthonormal columns of Definition 1."""
+    from oracle import transforms as tr
+    real = tr.hartley_entries
+    monkeypatch.setattr(tr, "hartley_entries", lambda k, p, n: real(k, p, n) / np.sqrt(float(n)))
+    O = tr.omega_matrix_t(300, 20, 2, "hartley")
+    assert np.abs(O.T @ O - np.eye(20)).max() > 1e-3
+
+
+def test_unsquared_colspace_error_is_caught():
+    """Reporting num/den without the square root disagrees with the dense definition."""
+    from oracle import projection as pr
+    n = 200
+    pts = np.random.default_rng(1).random((n, 2))
+    K = kk.kernel_matrix(pts, pts, kk.SE, 0.2, 1.0)
+    Q, _ = hh.qr(K @ om.omega_matrix(n, 16, 3))
+    e = pr.colspace_error(pts, kk.SE, 0.2, 1.0, Q, col_block=50)
+    dense = np.linalg.norm(K - Q @ Q.T @ K) / np.linalg.norm(K)
+    assert abs(e - dense) <= 1e-12 * dense
+    assert abs(e * e - dense) > 1e-6 * dense         # the planted slip would be visible
