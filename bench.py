@@ -391,6 +391,7 @@ def run_ours(args, rank, world, local_rank):
                            "tree_fp64_levels": args.fp64_levels, "parallelism": "replicas" if world > 1 else "1gpu",
                            "l2": "flushed between steps (256 MB write); Y and Q_hat (537 MB each) exceed L2"},
                 "tflops": achieved, "sketch_ms": sk_s * 1e3, "sketch_rel_err_sampled": y_err,
+                "kernel_evals_per_s": float(n) * float(n) / sk_s,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
