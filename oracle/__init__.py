@@ -16,7 +16,8 @@ Everything is float64 numpy.  Library primitives (matmul, sort, eigvalsh) serve 
 where noted; there is no blocking or fusion beyond what the paper states.
 
 Parity status per function (pins live in tests/test_oracle_*.py):
-  philox        pinned by statistics only (uniformity, independence of streams)
+  philox        pinned by the published known-answer vectors of Philox4x32-10, plus
+                uniformity and independence of the streams it draws
   kernels       pinned by Tables 1-2 (29.89, 38.18 and the order-of-magnitude rows)
                 and by the Bessel form of the Matern kernel at nu = 5/2
   omega         pinned by the Sylvester recursion of Sec. 3.2 and Omega^T Omega = I

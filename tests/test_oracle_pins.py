@@ -135,6 +135,23 @@ def test_omega_non_power_of_two_is_the_truncated_padded_matrix():
     assert np.array_equal(om.omega_matrix(n, d, 5), Ofull[:n])
 
 
+def test_philox_matches_the_published_known_answers():
+    """The generator behind R and P (Definition 1 draws them at random; Philox4x32-10 is the
+    reading) reproduces the known-answer vectors published with it, word for word."""
+    from oracle.philox import philox4x32_10, philox4x32_10_block
+    path = os.path.join(GOLDEN, "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = philox4x32_10_block(w[0], w[1], w[2], w[3], w[4], w[5])
+        assert [int(o) for o in out] == w[6:10]
+    # the counter layout used for the draws: (index_lo, index_hi, stream, 0), key = seed
+    c = philox4x32_10_block(5, 0, 1, 0, 7, 0)
+    d = philox4x32_10(np.array([5], dtype=np.uint64), 1, 7)
+    assert [int(x) for x in c] == [int(x[0]) for x in d]
+
+
 def test_rademacher_signs_are_balanced_and_stream_independent():
     n = 1 << 18
     s = om.rademacher_signs(n, 11)
