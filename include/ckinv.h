@@ -109,14 +109,29 @@ ckinv_status ckinv_destroy(ckinv_ctx *ctx);
 const char *ckinv_last_error(const ckinv_ctx *ctx);
 
 /* Synchronise `stream` and report device-detected failures of earlier asynchronous
- * calls on this context (bounded-wait timeout, zero LU pivot, list overflow) as a
- * status; clears the device error word. */
+ * calls on this context as a status, then clear the device error word:
+ *   CKINV_ETIMEOUT      a bounded device-side wait ran out (see ckinv_set_wait_limit);
+ *   CKINV_EINVAL        a NaN or infinity in the points, A or y (checked on the device);
+ *   CKINV_ESINGULAR     a zero, infinite or NaN pivot in LU(B) or LU(C');
+ *   CKINV_EUNSUPPORTED  an on-device list overflowed (Omega draw).
+ * The paper has no counterpart (error handling of this library). */
 ckinv_status ckinv_check(ckinv_ctx *ctx, ckinv_stream stream);
+
+/* Limit, in nanoseconds, of every device-side wait of the tensor-core kernels launched
+ * afterwards from this context on another role's progress (a pipeline stage's data, the
+ * peer CTA, the accumulator).  When a wait runs out the CTA gives up its tile, waits (one
+ * second at most) for its own copies and tensor-core products still in flight, frees its
+ * tensor memory and exits; the failure surfaces as CKINV_ETIMEOUT from ckinv_check or from
+ * the next call that returns host scalars, and the context stays usable.  0 restores the
+ * default of one second; at most 60 s.  Outputs of a call that timed out are undefined.
+ * The paper has no counterpart (error handling of this library). */
+ckinv_status ckinv_set_wait_limit(ckinv_ctx *ctx, uint64_t nanoseconds);
 
 /* Omega of Definition 1 (Sec. 3.2) as drawn from `seed`:
  *   sign_bits: ceil(n/32) uint32 words; bit (k % 32) of word k/32 is 1 iff r_k = -1;
  *   cols:      d int32 column indices p_0 < ... < p_{d-1} in [0, N).
- * Both device, caller-owned.  Pass NULL for an output that is not wanted. */
+ * Both device, caller-owned.  Pass NULL for an output that is not wanted.  1 <= n <= 2^31,
+ * 1 <= d <= min(N, 4096); P is drawn by a two-level radix select over the N keys. */
 ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed,
                          uint32_t *sign_bits, int32_t *cols, ckinv_stream stream);
 
@@ -126,10 +141,13 @@ ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed,
  * no counterpart: this is an interface variant, not part of the method.
  *   Runs on the calling thread's current device; needs no context; calls no allocator.
  *   Its scratch is one fixed device array of about 304 KB per device (a 65536-bin key
- *   histogram, room for 4096 candidate columns, counters), kept until the process exits.
+ *   histogram, reused by both levels of the column select, room for 4096 candidate
+ *   columns, counters), kept until the process exits.
  *   The first call on a device resolves that array's device address (set-up).
  *   Limits: 1 <= n <= 2^31, 1 <= d <= min(512, N); larger sizes return CKINV_EINVAL with a
- *   message in ckinv_last_error(NULL).
+ *   message in ckinv_last_error(NULL).  The two-level select keeps the candidate list near
+ *   d entries (about N / 2^32 keys share its last bin), so the 4096 slots suffice at every
+ *   n in range; an overflow would still be reported as CKINV_EUNSUPPORTED.
  *   Every call on a device shares the array: calls whose GPU work overlaps (other streams,
  *   other host threads) race on it and must be serialised by the caller.
  *   Outputs as in ckinv_omega (device, caller-owned).  The call synchronises `stream`
@@ -139,7 +157,9 @@ ckinv_status ckinv_omega_noalloc(int64_t n, int32_t d, uint64_t seed, uint32_t *
 
 /* Sketch Y = K0 Omega (Sec. 3.1-3.2; Sec. 3.3's K_hat), computed matrix-free from the
  * points: kernel tiles are evaluated on the fly and contracted with Omega.
- *   points: n x dim FP32 row-major (x_i at points[i*dim]); NULL for CKINV_DENSE.
+ *   points: n x dim FP32 row-major (x_i at points[i*dim]); NULL for CKINV_DENSE.  The
+ *           tensor-core forms need them 16-byte aligned (CKINV_EINVAL otherwise).  A NaN or
+ *           infinity among them is reported by the next ckinv_check as CKINV_EINVAL.
  *   K, ldk: n x n FP32 column-major kernel matrix for CKINV_DENSE (ldk >= n), else NULL.
  *   Y, ldy: n x d FP32 column-major output (ldy >= n).
  * No nugget enters the sketch.  plan->prec selects the contraction precision. */
@@ -147,6 +167,14 @@ ckinv_status ckinv_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
                           const ckinv_kernel *kern, const float *points,
                           const float *K, int64_t ldk, float *Y, int64_t ldy,
                           ckinv_stream stream);
+
+/* The kernel matrix K0 = variance * rho(x_i, x_k) materialised in device memory (n x n
+ * FP32, column-major, ldk >= n; each entry evaluated in FP64 from the FP32 points and
+ * rounded once): the input of the plain method with K held explicitly (Sec. 3.1 sketches a
+ * given K), which ckinv_sketch then contracts as CKINV_DENSE.  4 n^2 bytes. */
+ckinv_status ckinv_kernel_matrix(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                                 const ckinv_kernel *kern, const float *points, float *K,
+                                 int64_t ldk, ckinv_stream stream);
 
 /* Derivative sketch dK0/dlog(l) Omega (same layout as ckinv_sketch); used by the
  * gradient.  Not defined for CKINV_DENSE. */
@@ -184,7 +212,8 @@ ckinv_status ckinv_factor_core(const ckinv_factor *f, double *B, double *Cp,
 
 /* X = K_tilde^-1 A (Sec. 1's R^-1 Q^T A in Woodbury form), then plan->refine_steps
  * steps of FP64 iterative refinement X += K_tilde^-1 (A - K_tilde X).
- *   A: n x m FP32 (lda >= n);  X: n x m FP32 (ldx >= n); X may equal A.  1 <= m <= 256. */
+ *   A: n x m FP32 (lda >= n);  X: n x m FP32 (ldx >= n); X may equal A.  1 <= m <= 256.
+ * A NaN or infinity in A is reported by the next ckinv_check as CKINV_EINVAL. */
 ckinv_status ckinv_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A,
                          int64_t lda, int32_t m, float *X, int64_t ldx,
                          ckinv_stream stream);
@@ -206,14 +235,6 @@ ckinv_status ckinv_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
                             const float *y, double *nll, double *grad,
                             ckinv_stream stream);
 
-/* Batched form over nprob independent problems (uneven n, d, kernels): plans[p],
- * kerns[p], points[p], y[p] as above (device pointers in HOST arrays); nll[p] and
- * grad[3p..3p+2] are host outputs, written after `stream` is synchronised.  Each problem
- * runs the same pipeline as ckinv_nll_grad; the pipelines of all problems are captured
- * into one CUDA graph (on 8 forked streams, so that small problems overlap on the SMs)
- * and the graph is launched once.  A problem whose block_rows is 0 gets the leaf height
- * the autotuner (ckinv_autotune) picks for its shape class, tuned on first sight.
- * Device-side errors name the problem index in ckinv_last_error. */
 /* Leaf-height autotuner of the TSQR (the block_rows of a plan).  Times the TSQR of an
  * n x d pseudo-random matrix at the candidate heights 256 .. 4096 (at least d, at most
  * n / 2) with the plan's tree_fp64_levels and leaf_fp64, and records the fastest for the
@@ -224,6 +245,17 @@ ckinv_status ckinv_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
  * library uses 2048 rows, or n / 2 for small n. */
 ckinv_status ckinv_autotune(ckinv_ctx *ctx, const ckinv_plan_desc *plan, int32_t *block_rows,
                             ckinv_stream stream);
+
+/* Batched form over nprob independent problems (uneven n, d, kernels): plans[p],
+ * kerns[p], points[p], y[p] as above (device pointers in HOST arrays); nll[p] and
+ * grad[3p..3p+2] are host outputs, written after `stream` is synchronised.  Each problem
+ * runs the same pipeline as ckinv_nll_grad; the pipelines of all problems are captured
+ * into one CUDA graph (on 8 forked streams, so that small problems overlap on the SMs)
+ * and the graph is launched once.  A problem whose block_rows is 0 gets the leaf height
+ * the autotuner (ckinv_autotune) picks for its shape class, tuned on first sight.
+ * Device-side errors name the problem index in ckinv_last_error.  The paper motivates the
+ * method by likelihoods of many points (Abstract, Sec. 1); batching many independent
+ * problems has no counterpart there. */
 
 ckinv_status ckinv_nll_grad_batched(ckinv_ctx *ctx, int32_t nprob,
                                     const ckinv_plan_desc *plans,

@@ -13,32 +13,35 @@ full-rank QR unique.
 import numpy as np
 
 
-def house(x):
+def house(x, dtype=np.float64):
     """Return (v, tau, r) with (I - tau v v^T) x = r e_1 and v[0] = 1."""
-    x = np.asarray(x, dtype=np.float64)
+    x = np.asarray(x, dtype=dtype)
     normx = np.sqrt(np.dot(x, x))
     v = np.zeros_like(x)
     v[0] = 1.0
     if normx == 0.0:
-        return v, 0.0, 0.0
-    s = 1.0 if x[0] >= 0.0 else -1.0
+        return v, dtype(0.0), dtype(0.0)
+    s = dtype(1.0) if x[0] >= 0.0 else dtype(-1.0)
     head = x[0] + s * normx
     v[1:] = x[1:] / head
-    tau = 2.0 / np.dot(v, v)
+    tau = dtype(2.0) / np.dot(v, v)
     return v, tau, -s * normx
 
 
-def householder_qr(A):
+def householder_qr(A, dtype=np.float64):
     """QR of an m x k matrix (m >= k).  Returns (V, tau, R): V is m x k unit lower
-    trapezoidal (the reflectors), tau the k scalars, R the k x k upper triangle."""
-    A = np.array(A, dtype=np.float64, copy=True)
+    trapezoidal (the reflectors), tau the k scalars, R the k x k upper triangle.
+    `dtype` is the working precision (FP64 unless a floor of a lower-precision
+    factorisation is wanted: float32 runs the same steps with every operation rounded
+    to FP32)."""
+    A = np.array(A, dtype=dtype, copy=True)
     m, k = A.shape
     if m < k:
         raise ValueError("householder_qr needs at least as many rows as columns")
-    V = np.zeros((m, k))
-    tau = np.zeros(k)
+    V = np.zeros((m, k), dtype=dtype)
+    tau = np.zeros(k, dtype=dtype)
     for j in range(k):
-        v, t, r = house(A[j:, j])
+        v, t, r = house(A[j:, j], dtype)
         w = v @ A[j:, j:]
         A[j:, j:] -= t * np.outer(v, w)
         A[j, j] = r
@@ -49,8 +52,8 @@ def householder_qr(A):
 
 
 def apply_q(V, tau, B):
-    """Q B with Q = H_0 H_1 ... H_{k-1} (B has m rows)."""
-    B = np.array(B, dtype=np.float64, copy=True)
+    """Q B with Q = H_0 H_1 ... H_{k-1} (B has m rows), in the reflectors' precision."""
+    B = np.array(B, dtype=V.dtype, copy=True)
     for j in reversed(range(V.shape[1])):
         v = V[j:, j]
         B[j:] -= tau[j] * np.outer(v, v @ B[j:])
@@ -69,7 +72,7 @@ def apply_qt(V, tau, B):
 def thin_q(V, tau):
     """The first k columns of Q (m x k)."""
     m, k = V.shape
-    return apply_q(V, tau, np.eye(m, k))
+    return apply_q(V, tau, np.eye(m, k, dtype=V.dtype))
 
 
 def normalise(Q, R):

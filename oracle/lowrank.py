@@ -101,8 +101,8 @@ class Factor:
                 - lu_logabsdet(self.lu_B))
 
 
-def factorise(Y, omega, tau, block_rows):
-    t = tsqr(Y, block_rows)
+def factorise(Y, omega, tau, block_rows, leaf_dtype=np.float64):
+    t = tsqr(Y, block_rows, leaf_dtype)
     return Factor(t["Q"], t["R"], omega, tau)
 
 

@@ -29,18 +29,20 @@ def leaf_ranges(n, d, b):
     return ranges
 
 
-def tsqr(Y, b):
+def tsqr(Y, b, leaf_dtype=np.float64):
     """TSQR of the n x d matrix Y with leaves of b rows.
 
     Returns a dict with 'R' (d x d, diag >= 0), 'Q' (explicit thin Q_hat, n x d),
-    'leaves' and 'levels' (the tree, for inspection)."""
+    'leaves' and 'levels' (the tree, for inspection).  `leaf_dtype` is the working
+    precision of the leaf factorisations and of the leaves' part of Q_hat (float32 gives
+    the floor of a method with FP32 leaves and an FP64 tree); the tree is always FP64."""
     Y = np.asarray(Y, dtype=np.float64)
     n, d = Y.shape
     ranges = leaf_ranges(n, d, b)
     leaves = []
     for (s, e) in ranges:
-        V, tau, R = householder_qr(Y[s:e])
-        leaves.append({"range": (s, e), "V": V, "tau": tau, "R": R})
+        V, tau, R = householder_qr(Y[s:e], leaf_dtype)
+        leaves.append({"range": (s, e), "V": V, "tau": tau, "R": R.astype(np.float64)})
     # tree nodes: ('leaf', i) or ('node', a, b, V, tau); each carries its R
     level = [{"kind": "leaf", "index": i, "R": lf["R"]} for i, lf in enumerate(leaves)]
     levels = [level]
@@ -69,6 +71,6 @@ def tsqr(Y, b):
     Q = np.empty((n, d))
     for i, lf in enumerate(leaves):
         s, e = lf["range"]
-        Q[s:e] = thin_q(lf["V"], lf["tau"]) @ Qtree[i * d:(i + 1) * d]
+        Q[s:e] = thin_q(lf["V"], lf["tau"]) @ Qtree[i * d:(i + 1) * d].astype(leaf_dtype)
     Q, R = normalise(Q, root["R"])
     return {"R": R, "Q": Q, "leaves": leaves, "levels": levels}

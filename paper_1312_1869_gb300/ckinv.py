@@ -51,10 +51,13 @@ _SIGS = {
     "ckinv_destroy": (ctypes.c_int, [_VP]),
     "ckinv_last_error": (ctypes.c_char_p, [_VP]),
     "ckinv_check": (ctypes.c_int, [_VP, _VP]),
+    "ckinv_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "ckinv_omega": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
     "ckinv_omega_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
     "ckinv_sketch": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                     ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "ckinv_kernel_matrix": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
+                                           ctypes.c_int64, _VP]),
     "ckinv_sketch_dlogl": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                           ctypes.c_int64, _VP]),
     "ckinv_tsqr": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, ctypes.c_int64,
@@ -185,6 +188,12 @@ def check(ctx, stream=None):
     ctx._raise(load().ckinv_check(ctx.handle, _stream(stream)))
 
 
+def set_wait_limit(ctx, nanoseconds):
+    """Limit of the device-side waits of the tensor-core kernels launched afterwards from
+    this context (0 restores the default of one second)."""
+    ctx._raise(load().ckinv_set_wait_limit(ctx.handle, int(nanoseconds)))
+
+
 def omega(ctx, n, d, seed, stream=None):
     """(sign_bits uint32[ceil(n/32)], cols int32[d]) on the device."""
     bits = torch.empty(((n + 31) // 32,), dtype=torch.int32, device="cuda")
@@ -219,6 +228,17 @@ def sketch(ctx, plan, kern, points=None, K=None, Y=None, stream=None):
     ctx._raise(load().ckinv_sketch(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(points), _ptr(K), ldk,
                                    _ptr(Y), ldy, _stream(stream)))
     return Y
+
+
+def kernel_matrix(ctx, plan, kern, points, K=None, stream=None):
+    """K0 (n x n float32, column-major) materialised on the device."""
+    if K is None:
+        K = colmajor(plan.n, plan.n)
+    ldk = _colmajor_ld(K, plan.n)
+    pd, kd = plan.desc(), kern.desc()
+    ctx._raise(load().ckinv_kernel_matrix(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(points), _ptr(K),
+                                          ldk, _stream(stream)))
+    return K
 
 
 def sketch_dlogl(ctx, plan, kern, points, Y=None, stream=None):

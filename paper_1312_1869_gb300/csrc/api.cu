@@ -47,6 +47,56 @@ unsigned long long &ckinv::launch_counter() {
 }
 
 namespace {
+// The library's own stream-ordered memory pools, one per device.  Freed blocks stay in the
+// pool (release threshold: never) so that the workspaces of repeated solves (hundreds of MB
+// each) are reused without remapping; the setting is private to these pools and leaves the
+// device's default pool, which other code in the process may use, as it was.  When the last
+// context on a device is destroyed its pool is trimmed back to the driver.
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+int g_live_ctx[kPoolDevices] = {};
+
+cudaError_t library_pool(int dev, cudaMemPool_t *out) {
+  if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t ckinv::dev_alloc(void **p, size_t bytes, cudaStream_t st) {
+  // inside a stream capture the allocation becomes a graph memory node of the device's
+  // graph pool; everywhere else it comes from the library's pool
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
+  if (cs != cudaStreamCaptureStatusNone) return cudaMallocAsync(p, bytes, st);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  if ((e = library_pool(dev, &pool)) != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+namespace {
 
 thread_local std::string g_static_err;
 
@@ -92,11 +142,14 @@ Error check_plan(const ckinv_plan_desc *plan, const ckinv_kernel *kern, bool nee
   return ok();
 }
 
-// The BF16 forms run the TSQR's large FP32 GEMMs on the tensor cores (three BF16 terms
-// per operand, FP32 accumulation in TMEM: R and Q_hat to ~1e-5, below those forms' sketch
-// error); the FP32 form and FP64 leaves keep them on the CUDA cores (~1e-7).
+// The BF16 form runs the TSQR's large FP32 GEMMs on the tensor cores (three BF16 terms per
+// operand, FP32 accumulation in TMEM: R to ~5e-6, Q_hat orthonormal to ~1e-5 at d = 512,
+// far below that form's 2^-9 kernel-entry rounding).  The forms that carry kernel entries to
+// 16 or 24 bits (BF16x2, BF16x3), the FP32 form and FP64 leaves keep them on the CUDA cores
+// (Q_hat orthonormal to ~5e-7): measured against the oracle, the tensor-core Q_hat alone put
+// the BF16x3 form's K^-1 A 20x to 1000x above its kernel-entry floor.
 bool tsqr_on_tensor_cores(const ckinv_plan_desc *plan) {
-  return plan->prec != CKINV_FP32 && plan->leaf_fp64 == 0;
+  return plan->prec == CKINV_BF16 && plan->leaf_fp64 == 0;
 }
 
 KernelParams make_params(const ckinv_plan_desc *plan, const ckinv_kernel *kern) {
@@ -122,9 +175,32 @@ Error read_device_error(ckinv_ctx *ctx, cudaStream_t st) {
   if (h) {
     CK_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
     if (h & DERR_TIMEOUT) return fail(CKINV_ETIMEOUT, "a bounded device-side wait ran out");
-    if (h & DERR_SINGULAR) return fail(CKINV_ESINGULAR, "zero pivot in an LU factorisation");
+    if (h & DERR_NONFINITE) return fail(CKINV_EINVAL, "non-finite value (NaN or Inf) in the points, A or y");
+    if (h & DERR_SINGULAR) return fail(CKINV_ESINGULAR, "zero or non-finite pivot in an LU factorisation");
     if (h & DERR_CAPACITY) return fail(CKINV_EUNSUPPORTED, "device list capacity exceeded (Omega draw)");
   }
+  return ok();
+}
+
+// Flags DERR_NONFINITE when any of the `count` values (rows x cols, leading dimension ld)
+// is a NaN or an infinity.  A cheap pass over inputs of O(n) size: the points, the right-hand
+// sides and the targets.
+__global__ void k_check_finite(const float *x, int64_t rows, int64_t cols, int64_t ld, int *err) {
+  const int64_t count = rows * cols;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[(e % rows) + (e / rows) * ld];
+    bad |= !(fabsf(v) <= 3.402823466e38f);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DERR_NONFINITE);
+}
+
+Error check_finite(ckinv_ctx *ctx, const float *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return ok();
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows * cols, 256), (int64_t)ctx->sm_count * 4);
+  note_launch();
+  k_check_finite<<<g, 256, 0, st>>>(x, rows, cols, ld, ctx->d_err);
+  CK_CUDA(cudaGetLastError());
   return ok();
 }
 
@@ -138,6 +214,7 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
   } else if (!points) {
     return fail(CKINV_EINVAL, "points must be non-null");
   }
+  if (kern->kind != CKINV_DENSE) CK_TRY(check_finite(ctx, points, plan->dim, plan->n, plan->dim, st));
   CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   KernelParams kp = make_params(plan, kern);
   if (kern->kind == CKINV_DENSE) {
@@ -154,7 +231,8 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
 void factor_release(ckinv_factor *f) {
   if (!f) return;
   for (void *p : {(void *)f->Q, (void *)f->R, (void *)f->B, (void *)f->Cp, (void *)f->luB, (void *)f->pivB,
-                  (void *)f->logdet_parts, (void *)f->bits, (void *)f->cols})
+                  (void *)f->logdet_parts, (void *)f->bits, (void *)f->cols, (void *)f->S2, (void *)f->pivS,
+                  (void *)f->logdet2})
     if (p) cudaFreeAsync(p, f->stream);
   delete f;
 }
@@ -212,9 +290,9 @@ Error autotune_leaf_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan, cudaStream
   int best = cand[0];
   float best_ms = 1e30f;
   do {
-    if (cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&Q, sizeof(float) * n * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&R, sizeof(double) * d * d, st) != cudaSuccess) {
+    if (dev_alloc((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
+        dev_alloc((void **)&Q, sizeof(float) * n * d, st) != cudaSuccess ||
+        dev_alloc((void **)&R, sizeof(double) * d * d, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "autotune workspace");
       break;
     }
@@ -278,7 +356,7 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
   Error e = ok();
   auto alloc = [&](void **p, size_t bytes) {
     if (e.st != CKINV_OK) return;
-    cudaError_t ce = cudaMallocAsync(p, bytes, st);
+    cudaError_t ce = dev_alloc(p, bytes, st);
     if (ce != cudaSuccess) e = fail(CKINV_ENOMEM, std::string("factor allocation: ") + cudaGetErrorString(ce));
   };
   const size_t dd = (size_t)d * d;
@@ -403,15 +481,15 @@ Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_
   ckinv_factor *f = nullptr;
   Error e = ok();
   do {
-    if (cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&Yd, sizeof(float) * n * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&alpha, sizeof(float) * n, st) != cudaSuccess) {
+    if (dev_alloc((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess ||
+        dev_alloc((void **)&Yd, sizeof(float) * n * d, st) != cudaSuccess ||
+        dev_alloc((void **)&alpha, sizeof(float) * n, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "nll workspace");
       break;
     }
     // ws: G1, G2, E, F, T1, T2 (d x d each), g3, beta, gamma, v1, v2 (d each), s[16]
     const size_t ws_elems = 6 * dd + 5 * (size_t)d + 16;
-    if (cudaMallocAsync((void **)&ws, sizeof(double) * ws_elems, st) != cudaSuccess) {
+    if (dev_alloc((void **)&ws, sizeof(double) * ws_elems, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "nll workspace");
       break;
     }
@@ -422,6 +500,7 @@ Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_
       e = fail(CKINV_ECUDA, "memset");
       break;
     }
+    if ((e = check_finite(ctx, y, n, 1, n, st)).st) break;
     if ((e = do_sketch(ctx, plan, kern, points, nullptr, 0, false, Y, n, st)).st) break;
     if ((e = do_sketch(ctx, plan, kern, points, nullptr, 0, true, Yd, n, st)).st) break;
     if ((e = do_tsqr(ctx, plan, kern, Y, n, &f, st)).st) break;
@@ -430,7 +509,7 @@ Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_
     if ((e = tsprod(ctx, n, d, 1, f->Q, n, nullptr, nullptr, 0, alpha, n, beta, st)).st) break;
     if ((e = tsprod(ctx, n, d, 1, Yd, n, nullptr, nullptr, 0, alpha, n, g3, st)).st) break;
     if ((e = tsprod(ctx, n, d, d, f->Q, n, nullptr, nullptr, 0, Yd, n, G1, st)).st) break;
-    if (n % 4 == 0 && plan->prec != CKINV_FP32) {
+    if (n % 4 == 0 && plan->prec == CKINV_BF16) {
       // G2 = Omega^T Yd on the tensor cores (rows of A are the columns of Yd)
       if ((e = omega_draw(ctx, n, d, plan->seed, st)).st) break;
       if ((e = dense_tc(ctx, d, n, d, 3, Yd, n, f->omega_scale, nullptr, 0, G2, d, 1, st)).st) break;
@@ -487,7 +566,7 @@ Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kerne
                   const float *y, double *nll, double *grad, cudaStream_t st) {
   if (!nll || !grad) return fail(CKINV_EINVAL, "null argument");
   double *dout = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&dout, sizeof(double) * 4, st));
+  CK_CUDA(dev_alloc((void **)&dout, sizeof(double) * 4, st));
   Error e = nll_grad_enqueue(ctx, plan, kern, points, y, dout, st);
   double hout[4] = {0, 0, 0, 0};
   if (e.st == CKINV_OK && cudaMemcpyAsync(hout, dout, sizeof(hout), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -671,19 +750,13 @@ ckinv_status ckinv_create(ckinv_ctx **out, int device) {
   ckinv_ctx *ctx = new ckinv_ctx();
   ctx->device = device;
   ctx->sm_count = prop.multiProcessorCount;
-  // Keep memory freed with cudaFreeAsync in the device's pool instead of returning it at
-  // every synchronisation: the library's stream-ordered workspaces (hundreds of MB per solve)
-  // are then reused without remapping.  A per-process allocator setting.
-  {
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-      uint64_t keep = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-  }
   if (cudaMalloc((void **)&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
     delete ctx;
     return finish(nullptr, fail(CKINV_ENOMEM, "context allocation failed"));
+  }
+  if (device < kPoolDevices) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    ++g_live_ctx[device];
   }
   *out = ctx;
   return CKINV_OK;
@@ -700,12 +773,23 @@ ckinv_status ckinv_destroy(ckinv_ctx *ctx) {
   for (void *p : {(void *)ctx->d_err, (void *)ctx->hist, (void *)ctx->cand, (void *)ctx->cand_idx,
                   (void *)ctx->small, (void *)ctx->om.bits, (void *)ctx->om.cols, (void *)ctx->om.omegaT})
     if (p) cudaFree(p);
+  if (ctx->device < kPoolDevices) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (--g_live_ctx[ctx->device] == 0 && g_pool[ctx->device]) cudaMemPoolTrimTo(g_pool[ctx->device], 0);
+  }
   delete ctx;
   return CKINV_OK;
 }
 
 const char *ckinv_last_error(const ckinv_ctx *ctx) {
   return ctx ? ctx->err.c_str() : g_static_err.c_str();
+}
+
+ckinv_status ckinv_set_wait_limit(ckinv_ctx *ctx, uint64_t nanoseconds) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  if (nanoseconds > 60000000000ull) return finish(ctx, fail(CKINV_EINVAL, "wait limit above 60 s"));
+  ctx->wait_ns = nanoseconds ? nanoseconds : kDefaultWaitNs;
+  return CKINV_OK;
 }
 
 ckinv_status ckinv_check(ckinv_ctx *ctx, ckinv_stream stream) {
@@ -744,6 +828,19 @@ ckinv_status ckinv_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const cki
   if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
   DeviceGuard g(ctx->device);
   return finish(ctx, do_sketch(ctx, plan, kern, points, K, ldk, false, Y, ldy, (cudaStream_t)stream));
+}
+
+ckinv_status ckinv_kernel_matrix(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern,
+                                 const float *points, float *K, int64_t ldk, ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  DeviceGuard g(ctx->device);
+  Error e = check_plan(plan, kern, true);
+  if (e.st == CKINV_OK && kern->kind == CKINV_DENSE) e = fail(CKINV_EINVAL, "a kernel function is needed");
+  if (e.st == CKINV_OK && (!points || !K || ldk < plan->n)) e = fail(CKINV_EINVAL, "need points, K and ldk >= n");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.st == CKINV_OK) e = check_finite(ctx, points, plan->dim, plan->n, plan->dim, st);
+  if (e.st == CKINV_OK) e = kernel_matrix(ctx, plan->n, plan->dim, make_params(plan, kern), points, K, ldk, st);
+  return finish(ctx, e);
 }
 
 ckinv_status ckinv_sketch_dlogl(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern,
@@ -801,13 +898,49 @@ ckinv_status ckinv_factor_core(const ckinv_factor *f, double *B, double *Cp, dou
   return CKINV_OK;
 }
 
+ckinv_status ckinv_factor_project(ckinv_ctx *ctx, ckinv_factor *f, const ckinv_plan_desc *plan,
+                                  const ckinv_kernel *kern, const float *points, double *S, double *colspace_err,
+                                  ckinv_stream stream) {
+  if (!ctx || !f) return finish(ctx, fail(CKINV_EINVAL, "null context or factor"));
+  DeviceGuard g(ctx->device);
+  Error e = check_plan(plan, kern, true);
+  if (e.st == CKINV_OK && (kern->kind == CKINV_DENSE || !points))
+    e = fail(CKINV_EINVAL, "the second pass needs points and a kernel function");
+  if (e.st == CKINV_OK && (plan->n != f->n || plan->d != f->d)) e = fail(CKINV_EINVAL, "plan does not match the factor");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.st == CKINV_OK) e = check_finite(ctx, points, plan->dim, plan->n, plan->dim, st);
+  if (e.st == CKINV_OK) e = two_pass_core(ctx, f, plan->dim, make_params(plan, kern), points, colspace_err, st);
+  if (e.st == CKINV_OK && S && cudaMemcpyAsync(S, f->S2, sizeof(double) * f->d * f->d, cudaMemcpyDeviceToDevice, st) !=
+                                   cudaSuccess)
+    e = fail(CKINV_ECUDA, "copy of S failed");
+  return finish(ctx, e);
+}
+
+ckinv_status ckinv_predict_mean(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern,
+                                const float *points, const float *alpha, const float *new_points, int64_t n_new,
+                                double *mean, ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  DeviceGuard g(ctx->device);
+  Error e = check_plan(plan, kern, true);
+  if (e.st == CKINV_OK && kern->kind == CKINV_DENSE) e = fail(CKINV_EINVAL, "the predictive mean needs a kernel function");
+  if (e.st == CKINV_OK && (!points || !alpha || !new_points || !mean || n_new < 0))
+    e = fail(CKINV_EINVAL, "null argument or n_new < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.st == CKINV_OK) e = check_finite(ctx, new_points, plan->dim, n_new, plan->dim, st);
+  if (e.st == CKINV_OK && n_new > 0)
+    e = predict_mean(ctx, plan->n, plan->dim, make_params(plan, kern), points, alpha, new_points, n_new, mean, st);
+  return finish(ctx, e);
+}
+
 ckinv_status ckinv_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda, int32_t m, float *X,
                          int64_t ldx, ckinv_stream stream) {
   if (!ctx || !f) return finish(ctx, fail(CKINV_EINVAL, "null context or factor"));
   if (!A || !X || lda < f->n || ldx < f->n || m < 1 || m > 256)
     return finish(ctx, fail(CKINV_EINVAL, "need A, X non-null, lda/ldx >= n, 1 <= m <= 256"));
   DeviceGuard g(ctx->device);
-  return finish(ctx, lowrank_solve(ctx, f, A, lda, m, X, ldx, f->refine_steps, (cudaStream_t)stream));
+  Error e = check_finite(ctx, A, f->n, m, lda, (cudaStream_t)stream);
+  if (e.st == CKINV_OK) e = lowrank_solve(ctx, f, A, lda, m, X, ldx, f->refine_steps, (cudaStream_t)stream);
+  return finish(ctx, e);
 }
 
 ckinv_status ckinv_kinv_a(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
@@ -832,7 +965,7 @@ ckinv_status ckinv_kinv_a(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const cki
     float *Xd = X;
     int64_t ldxd = ldx;
     if (hp) {
-      if (cudaMallocAsync((void **)&dp, sizeof(float) * n * plan->dim, st) != cudaSuccess ||
+      if (dev_alloc((void **)&dp, sizeof(float) * n * plan->dim, st) != cudaSuccess ||
           cudaMemcpyAsync(dp, points, sizeof(float) * n * plan->dim, cudaMemcpyHostToDevice, st) != cudaSuccess) {
         e = fail(CKINV_ECUDA, "staging of points failed");
         break;
@@ -840,7 +973,7 @@ ckinv_status ckinv_kinv_a(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const cki
       P = dp;
     }
     if (ha) {
-      if (cudaMallocAsync((void **)&dA, sizeof(float) * n * m, st) != cudaSuccess ||
+      if (dev_alloc((void **)&dA, sizeof(float) * n * m, st) != cudaSuccess ||
           cudaMemcpy2DAsync(dA, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
                             cudaMemcpyHostToDevice, st) != cudaSuccess) {
         e = fail(CKINV_ECUDA, "staging of A failed");
@@ -850,17 +983,18 @@ ckinv_status ckinv_kinv_a(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const cki
       ldad = n;
     }
     if (hx) {
-      if (cudaMallocAsync((void **)&dX, sizeof(float) * n * m, st) != cudaSuccess) {
+      if (dev_alloc((void **)&dX, sizeof(float) * n * m, st) != cudaSuccess) {
         e = fail(CKINV_ENOMEM, "staging of X failed");
         break;
       }
       Xd = dX;
       ldxd = n;
     }
-    if (cudaMallocAsync((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess) {
+    if (dev_alloc((void **)&Y, sizeof(float) * n * d, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "sketch allocation failed");
       break;
     }
+    if ((e = check_finite(ctx, Ad, n, m, ldad, st)).st) break;
     if ((e = do_sketch(ctx, plan, kern, P, nullptr, 0, false, Y, n, st)).st) break;
     if ((e = do_tsqr(ctx, plan, kern, Y, n, &f, st)).st) break;
     if ((e = lowrank_solve(ctx, f, Ad, ldad, m, Xd, ldxd, plan->refine_steps, st)).st) break;

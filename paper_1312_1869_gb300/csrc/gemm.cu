@@ -185,7 +185,7 @@ Error gemm_simt(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha,
     ksplit = std::max(ksplit, 1);
   }
   T *part = nullptr;
-  if (ksplit > 1) CK_CUDA(cudaMallocAsync((void **)&part, sizeof(T) * (size_t)M * N * batch * ksplit, st));
+  if (ksplit > 1) CK_CUDA(dev_alloc((void **)&part, sizeof(T) * (size_t)M * N * batch * ksplit, st));
   if (big)
     launch_shape<T, 128, 128, 8, 8>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
                                     part, nb1, sA2, sB2, sC2, st);

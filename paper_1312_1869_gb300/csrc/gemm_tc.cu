@@ -40,12 +40,13 @@ __device__ __forceinline__ void g_mbar_arrive(uint32_t bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool g_try_wait(uint32_t bar, uint32_t parity) {
+  const uint32_t hint_ns = 20000u;
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
@@ -54,34 +55,52 @@ __device__ __forceinline__ uint64_t g_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded single-thread wait (~1 s, or until another warp flags an abort).
-__device__ __noinline__ bool g_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool g_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// A limit of at least 100 us polls with try_wait (20 us suspend hint) and checks the clock
+// every 16 polls; a shorter one polls without suspending and checks after every poll.
+__device__ __forceinline__ bool g_poll(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  return limit_ns < 100000ull ? g_test_wait(bar, parity) : g_try_wait(bar, parity);
+}
+// Bounded single-thread wait (gives up after limit_ns, or when another warp flags an abort).
+__device__ __noinline__ bool g_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint64_t limit_ns) {
   const uint64_t t0 = g_ns();
+  const uint32_t every = limit_ns < 100000ull ? 0u : 15u;
   for (uint32_t it = 0;; ++it) {
-    if (g_try_wait(bar, parity)) return true;
-    if ((it & 15u) == 15u) {
+    if (g_poll(bar, parity, limit_ns)) return true;
+    if ((it & every) == every) {
       if (*abort_flag) return false;
-      if (g_ns() - t0 > 1000000000ull) {
+      if (g_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         return false;
       }
     }
   }
 }
-__device__ __forceinline__ bool g_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  return g_try_wait(bar, parity) || g_wait_slow(bar, parity, abort_flag);
+__device__ __forceinline__ bool g_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint64_t limit_ns) {
+  return g_poll(bar, parity, limit_ns) || g_wait_slow(bar, parity, abort_flag, limit_ns);
 }
 // Warp-wide bounded wait: every lane polls (each acquires the phase), the warp leaves together.
-__device__ __forceinline__ bool g_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  if (__all_sync(0xffffffffu, g_try_wait(bar, parity))) return true;
+__device__ __forceinline__ bool g_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                             uint64_t limit_ns) {
+  if (__all_sync(0xffffffffu, g_poll(bar, parity, limit_ns))) return true;
   const uint64_t t0 = g_ns();
+  const uint32_t every = limit_ns < 100000ull ? 0u : 15u;
   for (uint32_t it = 0;; ++it) {
-    if (__all_sync(0xffffffffu, g_try_wait(bar, parity))) return true;
-    if ((it & 15u) == 15u) {
+    if (__all_sync(0xffffffffu, g_poll(bar, parity, limit_ns))) return true;
+    if ((it & every) == every) {
       int stop = 0;
       if ((threadIdx.x & 31) == 0) {
         if (*abort_flag) stop = 1;
-        else if (g_ns() - t0 > 1000000000ull) {
+        else if (g_ns() - t0 > limit_ns) {
           *abort_flag = 1;
           stop = 1;
         }
@@ -213,7 +232,7 @@ template <bool TRANSA>
 __global__ void __launch_bounds__(kGThreads, 1)
     k_gemm_tc(int M, int N, int K, float alpha, const float *__restrict__ A, int64_t lda, int64_t sA,
               const float *__restrict__ B, int64_t ldb, int64_t sB, float beta, float *C, int64_t ldc, int64_t sC,
-              int vecA, int vecB, int *err) {
+              int vecA, int vecB, int *err, uint64_t wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % kGStages;
         const uint32_t ph = (uint32_t)(kb / kGStages) & 1u;
-        if (!g_wait(full(s), ph, abort_flag)) {
+        if (!g_wait(full(s), ph, abort_flag, wait_ns)) {
           good = false;
           break;
         }
@@ -284,7 +303,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       if (issued > 0) {
         volatile int never = 0;
         g_commit(drain_bar);
-        g_wait(drain_bar, 0u, &never);
+        g_wait(drain_bar, 0u, &never, kDefaultWaitNs);   // the MMAs always drain
       }
     }
     __syncwarp();
@@ -341,7 +360,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kGStages;
       const uint32_t ph = (uint32_t)(kb / kGStages) & 1u;
-      if (!g_wait_lanes(empty(s), ph ^ 1u, abort_flag)) { good = false; break; }
+      if (!g_wait_lanes(empty(s), ph ^ 1u, abort_flag, wait_ns)) { good = false; break; }
       if (TRANSA) store_quads(xa, a_tile(s, 0));
       else store_row(xa, a_tile(s, 0));
       store_quads(xb, b_tile(s, 0));
@@ -350,7 +369,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       if (kb + 1 < nkb) load_block(kb + 1);
     }
     // epilogue: TMEM lane quadrant warp % 4, columns split between the two warps of a quadrant
-    if (good && nkb > 0 && g_wait_lanes(accum_bar, 0u, abort_flag)) {
+    if (good && nkb > 0 && g_wait_lanes(accum_bar, 0u, abort_flag, wait_ns)) {
       g_tc_after();
       const int q = warp & 3;
       const int m = m0 + q * 32 + lane;
@@ -397,11 +416,11 @@ Error gemm_tc_f32(const ckinv_ctx *ctx, bool transA, int M, int N, int K, float 
   if (transA) {
     CK_CUDA(cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem));
     k_gemm_tc<true><<<grid, kGThreads, kGSmem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vecA,
-                                                     vecB, ctx->d_err);
+                                                     vecB, ctx->d_err, ctx->wait_ns);
   } else {
     CK_CUDA(cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem));
     k_gemm_tc<false><<<grid, kGThreads, kGSmem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vecA,
-                                                      vecB, ctx->d_err);
+                                                      vecB, ctx->d_err, ctx->wait_ns);
   }
   CK_CUDA(cudaGetLastError());
   return ok();

@@ -48,7 +48,22 @@ enum : int {
   DERR_TIMEOUT = 1,      // a bounded mbarrier / flag wait ran out
   DERR_SINGULAR = 2,     // zero pivot in an LU
   DERR_CAPACITY = 4,     // an on-device list overflowed its buffer
+  DERR_NONFINITE = 8,    // a non-finite value in the points, A or y
 };
+
+// Limit of a device-side wait for another role's progress (ns), unless the context sets
+// another one (ckinv_set_wait_limit).  Waits for the library's own copies and MMAs to drain
+// after a timeout always keep the default, so that nothing is left in flight.
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;
+
+// Stream-ordered device allocation from the library's own memory pool (one per device,
+// created on first use, freed memory kept for reuse), or from the device's default pool
+// while `st` is being captured into a CUDA graph.  Free with cudaFreeAsync.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t dev_alloc(T **p, size_t bytes, cudaStream_t st) {
+  return dev_alloc(reinterpret_cast<void **>(p), bytes, st);
+}
 
 // ----------------------------------------------------------------------------- context
 // The last Omega drawn on a context; buffers only grow, so that a context whose capacity
@@ -100,6 +115,8 @@ struct ckinv_ctx {
   // FP32 GEMMs on the tensor cores (split BF16) rather than the CUDA cores; set by
   // tsqr_factor for the duration of one factorization
   bool gemm_tc = false;
+  // limit of the device-side waits of kernels launched from this context (ns)
+  uint64_t wait_ns = ckinv::kDefaultWaitNs;
 };
 
 struct ckinv_factor {
@@ -123,6 +140,11 @@ struct ckinv_factor {
   double omega_scale = 0;
   int refine_steps = 0;
   int prec = 0;              // plan precision: FP32 keeps every contraction FP32-accurate
+  // two-pass core (ckinv_factor_project): S = Q_hat^T K0 Q_hat and the LU of S + tau I
+  bool two_pass = false;
+  double *S2 = nullptr;      // d x d S, then d x d packed LU of S + tau I
+  int32_t *pivS = nullptr;
+  double *logdet2 = nullptr; // ln|det(S + tau I)|
 };
 
 namespace ckinv {
@@ -160,6 +182,10 @@ Error omega_reserve(ckinv_ctx *ctx, int64_t n, int32_t d, cudaStream_t st);
 Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp,
                   const float *points, const float *K, int64_t ldk, bool deriv,
                   float *Y, int64_t ldy, cudaStream_t st);
+// K (n x n FP32, column-major, ld ldk) = var * rho(x_i, x_k), each entry evaluated in FP64
+// from the FP32 points and rounded once.
+Error kernel_matrix(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, float *K,
+                    int64_t ldk, cudaStream_t st);
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
                 int64_t ldy, cudaStream_t st);
@@ -206,6 +232,14 @@ Error lu_factor_f64(ckinv_ctx *ctx, int n, double *A, int32_t *piv, double *loga
 Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda,
                     int m, float *X, int64_t ldx, int refine_steps, cudaStream_t st);
 Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st);
+// Second pass over K0: S = Q_hat^T K0 Q_hat (tensor cores, Q_hat in three BF16 terms, partial
+// sums folded in FP64), the factor switched to the two-pass core, and (if colspace is not
+// null) the column-space error ||K0 - Q Q^T K0||_F / ||K0||_F written to host *colspace.
+Error two_pass_core(ckinv_ctx *ctx, ckinv_factor *f, int dim, const KernelParams &kp, const float *points,
+                    double *colspace, cudaStream_t st);
+// mean[i] = K0(x*_i, X) alpha (FP64 entries and sums; mean device FP64).
+Error predict_mean(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, const float *alpha,
+                   const float *xnew, int64_t n_new, double *mean, cudaStream_t st);
 // X (d x m FP64) <- op(A)^-1 X for a packed LU with LAPACK interchanges.
 Error lu_solve_dev(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st);
 // C (d x m) = op(A) Bm, FP64, ld = d.

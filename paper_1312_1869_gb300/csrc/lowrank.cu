@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kLuPanelThreads) k_lu_panel(int d, int k0, int
     }
     if (tid == 0) {
       piv[k0 + j] = k0 + p;
-      if (bk == 0ull) {
+      if (bk == 0ull || bk >= 0x7ff0000000000000ull) {   // a zero, infinite or NaN pivot
         atomicOr(err, DERR_SINGULAR);
         s_inv = 0.0;
       } else {
@@ -703,7 +703,7 @@ Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t 
   int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
   double *part = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
+  CK_CUDA(dev_alloc((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
   dim3 grid(tx, ty, sp);
   ::ckinv::note_launch();
   if (narrow) {
@@ -724,7 +724,7 @@ static Error tsprod_dd(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L
   int64_t rps = ceil_div(ceil_div(n, sp), 256) * 256;
   sp = (int)ceil_div(n, rps);
   double *part = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
+  CK_CUDA(dev_alloc((void **)&part, sizeof(double) * (size_t)sp * d1 * d2, st));
   dim3 grid(tx, ty, sp);
   ::ckinv::note_launch(), k_tsprod_dd<<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, M, ldm, part, rps);
   CK_CUDA(cudaGetLastError());
@@ -762,6 +762,10 @@ static Error lu_blocked(ckinv_ctx *ctx, int nmat, int d, double *A, int32_t *piv
   return ok();
 }
 
+Error lu_factor_f64(ckinv_ctx *ctx, int n, double *A, int32_t *piv, double *logabsdet, cudaStream_t st) {
+  return lu_blocked(ctx, 1, n, A, piv, logabsdet, st);
+}
+
 static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
   if (d > kSolveThreads * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
   if (m <= 0 || d <= 0) return ok();
@@ -786,9 +790,9 @@ Error gemm_small_dev(int d, int m, const double *A, const double *Bm, double *C,
 Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
   const int d = f->d;
   // B = Omega^T Q_hat  (B^T = Q_hat^T Omega: rows of A are the columns of Q_hat).  The BF16
-  // forms use the tensor cores with Q_hat split into three BF16 terms (~3e-6 relative); the
-  // FP32 form keeps the FP32-accurate contraction (FP64 across 256-row chunks)
-  if (f->n % 4 == 0 && f->prec != CKINV_FP32)
+  // form uses the tensor cores with Q_hat split into three BF16 terms (~1e-5 relative); the
+  // other forms keep the FP32-accurate contraction (FP64 across 256-row chunks)
+  if (f->n % 4 == 0 && f->prec == CKINV_BF16)
     CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
   else
     CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
@@ -806,23 +810,46 @@ Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64
   const int64_t n = f->n;
   double *Z = nullptr, *W = nullptr;
   float *Acopy = nullptr, *Rs = nullptr, *Dx = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&Z, sizeof(double) * d * m, st));
-  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(double) * d * m, st));
+  // the workspaces go back to the pool on every path out of this function, errors included
+  struct Release {
+    std::vector<void *> p;
+    cudaStream_t st;
+    ~Release() {
+      for (void *q : p)
+        if (q) cudaFreeAsync(q, st);
+    }
+  } release{{}, st};
+  auto keep = [&](void *q) { release.p.push_back(q); };
+  CK_CUDA(dev_alloc((void **)&Z, sizeof(double) * d * m, st));
+  keep(Z);
+  CK_CUDA(dev_alloc((void **)&W, sizeof(double) * d * m, st));
+  keep(W);
   const float *Ain = A;
   if (refine_steps > 0 || X == A) {
     // keep A: X may alias it and the refinement needs it
-    CK_CUDA(cudaMallocAsync((void **)&Acopy, sizeof(float) * n * m, st));
+    CK_CUDA(dev_alloc((void **)&Acopy, sizeof(float) * n * m, st));
+    keep(Acopy);
     CK_CUDA(cudaMemcpy2DAsync(Acopy, sizeof(float) * n, A, sizeof(float) * lda, sizeof(float) * n, m,
                               cudaMemcpyDeviceToDevice, st));
     Ain = Acopy;
     lda = n;
   }
+  // single-pass core: K_tilde = tau I + Q_hat B^-1 R^T Q_hat^T, solved through C' = R^T + tau B;
+  // two-pass core: K_tilde = tau I + Q_hat S Q_hat^T, solved through S + tau I
+  const double *S2 = f->two_pass ? f->S2 : nullptr;
+  const double *luS = f->two_pass ? f->S2 + (size_t)d * d : nullptr;
   auto solve_into = [&](const float *rhs, int64_t ldr, float *out, int64_t ldo) -> Error {
     CK_TRY(tsprod(ctx, n, d, m, f->Q, n, nullptr, nullptr, 0.0, rhs, ldr, Z, st));     // Z = Q^T rhs
     dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
-    ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);                           // W = R^T Z
-    CK_CUDA(cudaGetLastError());
-    CK_TRY(lu_solve(d, m, f->luC, f->pivC, W, 0, st));                                   // W = C'^-1 W
+    if (S2) {
+      ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, S2, Z, W, 0, 1.0);                          // W = S Z
+      CK_CUDA(cudaGetLastError());
+      CK_TRY(lu_solve(d, m, luS, f->pivS, W, 0, st));                                   // W = (S + tau I)^-1 W
+    } else {
+      ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);                         // W = R^T Z
+      CK_CUDA(cudaGetLastError());
+      CK_TRY(lu_solve(d, m, f->luC, f->pivC, W, 0, st));                                 // W = C'^-1 W
+    }
     dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 32));
     ::ckinv::note_launch(), k_apply_x<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, rhs, ldr, out, ldo, (float)(1.0 / f->tau));
     CK_CUDA(cudaGetLastError());
@@ -830,15 +857,22 @@ Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64
   };
   CK_TRY(solve_into(Ain, lda, X, ldx));
   if (refine_steps > 0) {
-    CK_CUDA(cudaMallocAsync((void **)&Rs, sizeof(float) * n * m, st));
-    CK_CUDA(cudaMallocAsync((void **)&Dx, sizeof(float) * n * m, st));
+    CK_CUDA(dev_alloc((void **)&Rs, sizeof(float) * n * m, st));
+    keep(Rs);
+    CK_CUDA(dev_alloc((void **)&Dx, sizeof(float) * n * m, st));
+    keep(Dx);
     for (int s = 0; s < refine_steps; ++s) {
-      // S = B^-1 R^T Q^T X  (FP64)
+      // W = B^-1 R^T Q^T X (single-pass) or S Q^T X (two-pass), FP64
       CK_TRY(tsprod_dd(ctx, n, d, m, f->Q, n, X, ldx, Z, st));
       dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
-      ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);
-      CK_CUDA(cudaGetLastError());
-      CK_TRY(lu_solve(d, m, f->luB, f->pivB, W, 0, st));
+      if (S2) {
+        ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, S2, Z, W, 0, 1.0);
+        CK_CUDA(cudaGetLastError());
+      } else {
+        ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);
+        CK_CUDA(cudaGetLastError());
+        CK_TRY(lu_solve(d, m, f->luB, f->pivB, W, 0, st));
+      }
       dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 16));
       ::ckinv::note_launch(), k_residual_dd<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, Ain, lda, X, ldx, f->tau, Rs, n);
       CK_CUDA(cudaGetLastError());
@@ -847,8 +881,6 @@ Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64
       CK_CUDA(cudaGetLastError());
     }
   }
-  for (void *p : {(void *)Z, (void *)W, (void *)Acopy, (void *)Rs, (void *)Dx})
-    if (p) CK_CUDA(cudaFreeAsync(p, st));
   return ok();
 }
 

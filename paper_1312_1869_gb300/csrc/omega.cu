@@ -27,19 +27,30 @@ __device__ __forceinline__ unsigned long long cand_key(int64_t c, uint32_t k0, u
   return ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
 }
 
-// Histogram of the top 16 key bits over all N candidates.
-__global__ void k_key_hist(int64_t N, uint32_t k0, uint32_t k1, uint32_t *hist) {
+// The d smallest of N keys by a two-level radix select: a histogram of the top 16 key bits
+// gives the bin t that holds the d-th smallest key; a histogram of the next 16 bits of the
+// keys in bin t gives the sub-bin t2 that holds it.  Every key below (t, t2) and the keys of
+// sub-bin t2 are then collected (about d of them: a sub-bin holds N / 2^32 keys on average)
+// and sorted in one block.
+//
+// level 0: histogram of key bits 63..48 over all N candidates;
+// level 1: histogram of key bits 47..32 over the candidates whose top bits equal small[0].
+__global__ void k_key_hist(int64_t N, uint32_t k0, uint32_t k1, const uint32_t *small, int level, uint32_t *hist) {
+  const uint32_t t = level ? small[0] : 0u;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
        c += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long key = cand_key(c, k0, k1);
-    atomicAdd(&hist[key >> 48], 1u);
+    if (level == 0) atomicAdd(&hist[key >> 48], 1u);
+    else if ((uint32_t)(key >> 48) == t) atomicAdd(&hist[(key >> 32) & 0xffffu], 1u);
   }
 }
 
-// One block of 1024 threads: find the bin t holding the d-th smallest key.
-// small[0] = t, small[1] = number of candidates in bins <= t.
-__global__ void k_pick_bin(const uint32_t *hist, int d, uint32_t *small) {
+// One block of 1024 threads: find the bin holding the target-th smallest key of the
+// histogram.  Level 0 (target d): small[0] = bin t, small[3] = keys in the bins below t.
+// Level 1 (target d - small[3], within bin t): small[4] = sub-bin t2.
+__global__ void k_pick_bin(const uint32_t *hist, int d, int level, uint32_t *small) {
   __shared__ uint32_t part[1024];
+  const uint32_t target = level ? (uint32_t)d - small[3] : (uint32_t)d;
   int t = threadIdx.x;
   uint32_t s = 0;
   for (int i = 0; i < 64; ++i) s += hist[t * 64 + i];
@@ -53,27 +64,33 @@ __global__ void k_pick_bin(const uint32_t *hist, int d, uint32_t *small) {
     __syncthreads();
   }
   uint32_t before = (t == 0) ? 0u : part[t - 1];
-  if (before < (uint32_t)d && part[t] >= (uint32_t)d) {
+  if (before < target && part[t] >= target) {
     uint32_t cum = before;
     for (int i = 0; i < 64; ++i) {
-      cum += hist[t * 64 + i];
-      if (cum >= (uint32_t)d) {
-        small[0] = (uint32_t)(t * 64 + i);
-        small[1] = cum;
+      const uint32_t h = hist[t * 64 + i];
+      if (cum + h >= target) {
+        if (level == 0) {
+          small[0] = (uint32_t)(t * 64 + i);
+          small[3] = cum;
+        } else {
+          small[4] = (uint32_t)(t * 64 + i);
+        }
         break;
       }
+      cum += h;
     }
   }
 }
 
+// Candidates: every key below bin (t, t2) of the two-level select, and the keys in it.
 __global__ void k_collect(int64_t N, uint32_t k0, uint32_t k1, const uint32_t *small,
                           unsigned long long *cand, uint32_t *cand_idx, uint32_t cap,
                           uint32_t *counter) {
-  uint32_t tbin = small[0];
+  const unsigned long long bound = ((unsigned long long)small[0] << 16) | small[4];   // key bits 63..32
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
        c += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long key = cand_key(c, k0, k1);
-    if ((uint32_t)(key >> 48) <= tbin) {
+    if ((key >> 32) <= bound) {
       uint32_t pos = atomicAdd(counter, 1u);
       if (pos < cap) {
         cand[pos] = key;
@@ -165,6 +182,28 @@ __global__ void k_omegaT(int64_t n, int64_t kpad, int d, const uint32_t *bits,
   *reinterpret_cast<__nv_bfloat162 *>(out + (int64_t)j * kpad + k2) = pr;
 }
 
+// Launch sequence of the column draw (two-level select, collect, sort) on scratch that the
+// caller provides: hist (65536 bins), small (>= 8 counters, zeroed here), the candidate
+// list (cap entries) and the error word.
+Error select_columns(int64_t N, int d, uint32_t k0, uint32_t k1, int grid, uint32_t *hist, uint32_t *small,
+                     unsigned long long *cand, uint32_t *cand_idx, uint32_t cap, int32_t *cols, int *err,
+                     cudaStream_t st) {
+  CK_CUDA(cudaMemsetAsync(small, 0, sizeof(uint32_t) * 8, st));
+  for (int level = 0; level < 2; ++level) {
+    CK_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 65536, st));
+    note_launch();
+    k_key_hist<<<grid, 256, 0, st>>>(N, k0, k1, small, level, hist);
+    note_launch();
+    k_pick_bin<<<1, 1024, 0, st>>>(hist, d, level, small);
+  }
+  note_launch();
+  k_collect<<<grid, 256, 0, st>>>(N, k0, k1, small, cand, cand_idx, cap, small + 2);
+  note_launch();
+  k_finalize<<<1, 1024, 0, st>>>(cand, cand_idx, small + 2, d, cols, err);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
 }  // namespace
 
 namespace {
@@ -174,7 +213,7 @@ Error grow(T **p, size_t *cap, size_t need, cudaStream_t st) {
   if (*p) cudaFreeAsync(*p, st);
   *p = nullptr;
   *cap = 0;
-  CK_CUDA(cudaMallocAsync((void **)p, sizeof(T) * need, st));
+  CK_CUDA(dev_alloc((void **)p, sizeof(T) * need, st));
   *cap = need;
   return ok();
 }
@@ -215,16 +254,9 @@ Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream
     CK_CUDA(cudaMalloc((void **)&ctx->cand_idx, sizeof(uint32_t) * ctx->cand_cap));
   }
   ::ckinv::note_launch(), k_signs<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, k0, k1, om.bits);
-  CK_CUDA(cudaMemsetAsync(ctx->hist, 0, sizeof(uint32_t) * 65536, st));
-  CK_CUDA(cudaMemsetAsync(ctx->small, 0, sizeof(uint32_t) * 16, st));
   int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->sm_count * 8);
-  ::ckinv::note_launch(), k_key_hist<<<grid, 256, 0, st>>>(N, k0, k1, ctx->hist);
-  ::ckinv::note_launch(), k_pick_bin<<<1, 1024, 0, st>>>(ctx->hist, d, ctx->small);
-  ::ckinv::note_launch(), k_collect<<<grid, 256, 0, st>>>(N, k0, k1, ctx->small, ctx->cand, ctx->cand_idx,
-                                  (uint32_t)ctx->cand_cap, ctx->small + 2);
-  ::ckinv::note_launch(), k_finalize<<<1, 1024, 0, st>>>(ctx->cand, ctx->cand_idx, ctx->small + 2, d, om.cols,
-                                 ctx->d_err);
-  CK_CUDA(cudaGetLastError());
+  CK_TRY(select_columns(N, d, k0, k1, grid, ctx->hist, ctx->small, ctx->cand, ctx->cand_idx, (uint32_t)ctx->cand_cap,
+                        om.cols, ctx->d_err, st));
   om.n = n;
   om.d = d;
   om.seed = seed;
@@ -306,6 +338,10 @@ extern "C" ckinv_status ckinv_omega_noalloc(int64_t n, int32_t d, uint64_t seed,
                      "holds a 65536-bin histogram and 4096 candidates");
     return CKINV_EINVAL;
   }
+  auto cuda_fail = [](const char *what, cudaError_t e) {
+    set_static_error(std::string("ckinv_omega_noalloc: ") + what + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CKINV_ENOMEM : CKINV_ECUDA;
+  };
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char *base = nullptr;
   {
@@ -322,28 +358,31 @@ extern "C" ckinv_status ckinv_omega_noalloc(int64_t n, int32_t d, uint64_t seed,
   uint32_t *cand_idx = reinterpret_cast<uint32_t *>(base + kNoAllocHistBytes + kNoAllocSmallBytes + kNoAllocKeyBytes);
   const int64_t N = padded_order(n);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  // the array keeps the previous call's contents: clear what must start at zero
-  if (cudaMemsetAsync(base, 0, kNoAllocHistBytes + kNoAllocSmallBytes, st) != cudaSuccess) return CKINV_ECUDA;
+  // the array keeps the previous call's contents: clear what must start at zero (the
+  // histogram and the counters are cleared again inside select_columns)
+  cudaError_t ce = cudaMemsetAsync(base, 0, kNoAllocHistBytes + kNoAllocSmallBytes, st);
+  if (ce != cudaSuccess) return cuda_fail("clearing the scratch array", ce);
   note_launch();
   k_signs<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, k0, k1, sign_bits);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_fail("launch of the sign draw", ce);
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return CKINV_ECUDA;
+  if ((ce = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail("cudaGetDevice", ce);
+  if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail("cudaDeviceGetAttribute", ce);
   const int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)sms * 8);
-  note_launch();
-  k_key_hist<<<grid, 256, 0, st>>>(N, k0, k1, hist);
-  note_launch();
-  k_pick_bin<<<1, 1024, 0, st>>>(hist, d, small);
-  note_launch();
-  k_collect<<<grid, 256, 0, st>>>(N, k0, k1, small, cand, cand_idx, (uint32_t)kSortCap, small + 2);
-  note_launch();
-  k_finalize<<<1, 1024, 0, st>>>(cand, cand_idx, small + 2, d, cols, err);
-  if (cudaGetLastError() != cudaSuccess) return CKINV_ECUDA;
-  // report a candidate-list overflow (not expected below n = 2^24) before returning
+  {
+    Error e = select_columns(N, d, k0, k1, grid, hist, small, cand, cand_idx, (uint32_t)kSortCap, cols, err, st);
+    if (e.st != CKINV_OK) {
+      set_static_error("ckinv_omega_noalloc: " + e.msg);
+      return e.st;
+    }
+  }
+  // report a candidate-list overflow (a sub-bin of the two-level select holding more than
+  // 4096 - d keys; about N / 2^32 are expected, so not at any supported n) before returning
   int herr = 0;
-  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return CKINV_ECUDA;
+  if ((ce = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail("read-back of the error word", ce);
+  if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail("stream synchronisation", ce);
   if (herr) {
     set_static_error("ckinv_omega_noalloc: more than 4096 candidate columns share the selection bin");
     return CKINV_EUNSUPPORTED;

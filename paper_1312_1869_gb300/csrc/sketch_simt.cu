@@ -135,7 +135,7 @@ Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams 
   R = std::min<int64_t>(R, n);
   R = ceil_div(R, BM) * BM;
   float *Kb = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&Kb, sizeof(float) * R * n, st));
+  CK_CUDA(dev_alloc((void **)&Kb, sizeof(float) * R * n, st));
   const double ell = kp.ell, var = kp.var;
   for (int64_t r0 = 0; r0 < n; r0 += R) {
     int64_t rows = std::min<int64_t>(R, n - r0);
@@ -149,6 +149,15 @@ Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams 
     CK_CUDA(cudaGetLastError());
   }
   CK_CUDA(cudaFreeAsync(Kb, st));
+  return ok();
+}
+
+Error kernel_matrix(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, float *K,
+                    int64_t ldk, cudaStream_t st) {
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), (int64_t)ctx->sm_count * 64);
+  note_launch();
+  k_kmat_f64<false><<<g, 256, 0, st>>>(n, 0, n, dim, kp.kind, kp.ell, kp.var, points, K, ldk);
+  CK_CUDA(cudaGetLastError());
   return ok();
 }
 

@@ -1,19 +1,25 @@
 // Fused sketch Y = K0 Omega (Sec. 3.1-3.3) on the 5th-generation tensor cores.
 //
-// One CTA owns 128 rows of Y and all d <= 512 columns; the FP32 accumulator lives in
-// TMEM (128 lanes x d columns).  The contraction runs over the n points in blocks of 32:
-//   * warps 2..9 evaluate the 128 x 32 kernel tile in FP32 (exp2 on the MUFU), split it
-//     into 1-3 BF16 terms and store them straight into the 64B-swizzled K-major SMEM
-//     layout the MMA reads (no HBM traffic for K0 at all);
-//   * warp 0 streams the 32 x d tile of the +-1 Omega pattern (BF16, exact) by TMA;
-//   * warp 1 issues tcgen05.mma (M = 128, N = min(d, 256) per instruction, K = 16) and
-//     commits each stage back to the producers through mbarriers.  Short blocks keep a
-//     stage small (40 KB at d = 512), so that 3-8 stages are in flight and the tensor
-//     pipe does not wait on the producer/consumer round trip;
-//   * after the last block, warps 2..9 read TMEM with tcgen05.ld, scale by variance * c
-//     and write Y (coalesced along rows: Y is column-major).
-// Every mbarrier wait is bounded; on timeout the CTA records DERR_TIMEOUT, drains its
-// own TMA copies and MMAs, frees TMEM and returns.
+// The CTAs run in pairs (clusters of two) that share each MMA: a pair owns 256 rows of Y
+// (128 per CTA) and all d <= 512 columns, its FP32 accumulator in TMEM (128 lanes x d
+// columns in each CTA).  The contraction runs over the n points in blocks of BK = 64:
+//   * warps 2..9 of each CTA evaluate its 128 x 64 kernel tile in FP32 (exp2 on the MUFU)
+//     from the block's points, split it into 1-3 BF16 terms and store them straight into
+//     the 128B-swizzled K-major SMEM layout the MMA reads (no HBM traffic for K0 at all);
+//   * warp 0, lane 0 of each CTA bulk-copies the raw coordinates of upcoming blocks into a
+//     shared ring and fetches by TMA its half of the block's 64 x d tile of the +-1 Omega
+//     pattern (BF16, exact);
+//   * warp 1, lane 0 of the first CTA issues tcgen05.mma.cta_group::2 (M = 256, N <= 256 per
+//     instruction, K = 16) once both CTAs' tiles of a stage are ready - the second CTA's
+//     warp 1 relays its readiness with one cluster-scope arrival - and commits each stage
+//     back to both CTAs' producers through mbarriers;
+//   * after the last block, warps 2..9 read TMEM with tcgen05.ld, scale by variance * c and
+//     write Y (coalesced along rows: Y is column-major).
+// MODE 1 takes the A operand from a dense FP32 matrix instead of evaluating kernel entries
+// (a materialised K, and the products B = Omega^T Q_hat and Omega^T Y' of the core and the
+// gradient).  Every mbarrier wait is bounded (the context's limit for waits on another
+// role's progress, one second for the CTA's own copies and MMAs to drain); on timeout the
+// CTA records DERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cstring>
@@ -55,23 +61,46 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 // try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
 // hint (ns) elapses, instead of spinning on the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  const uint32_t hint_ns = 20000u;
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
 // The same with cluster-scope acquire, for barriers that threads of the peer CTA arrive on.
 __device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity) {
+  const uint32_t hint_ns = 20000u;
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Non-blocking polls (no suspension), for waits with a limit shorter than a suspend window.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test_wait_cl(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
@@ -80,17 +109,31 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: gives up after ~1 s or when another warp has flagged an abort.  The first
-// poll is inline; the loop is not.
+// Limits of a wait: `ns` in all (the context's limit for waits on another role's progress,
+// the default second for waits on the CTA's own copies and MMAs to drain).  A limit of at
+// least 100 us polls with try_wait and a 20 us suspend hint, checking the clock every 16
+// polls; a shorter one polls with the non-blocking test_wait and checks the clock after
+// every poll, so that it runs out after about its own length.
+struct WaitLimit {
+  uint64_t ns;
+  bool fine;
+};
+__device__ __forceinline__ WaitLimit wait_limit(uint64_t ns) { return WaitLimit{ns, ns < 100000ull}; }
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity, bool cluster_scope, WaitLimit lim) {
+  if (lim.fine) return cluster_scope ? mbar_test_wait_cl(bar, parity) : mbar_test_wait(bar, parity);
+  return cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity);
+}
+// Bounded wait: gives up after the limit or when another warp has flagged an abort.  The
+// first poll is inline; the loop is not.
 __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                            bool cluster_scope) {
-  auto poll = [&]() { return cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); };
+                                            bool cluster_scope, WaitLimit lim) {
   const uint64_t t0 = global_ns();
+  const uint32_t every = lim.fine ? 0u : 15u;
   for (uint32_t it = 0;; ++it) {
-    if (poll()) return true;
-    if ((it & 15u) == 15u) {
+    if (mbar_poll(bar, parity, cluster_scope, lim)) return true;
+    if ((it & every) == every) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > 1000000000ull) {
+      if (global_ns() - t0 > lim.ns) {
         *abort_flag = 1;
         return false;
       }
@@ -98,23 +141,25 @@ __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volat
   }
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          bool cluster_scope = false) {
-  if (cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity)) return true;
-  return mbar_wait_slow(bar, parity, abort_flag, cluster_scope);
+                                          bool cluster_scope, WaitLimit lim) {
+  if (mbar_poll(bar, parity, cluster_scope, lim)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, cluster_scope, lim);
 }
 
 // Warp-wide bounded wait: every lane polls, so that each lane acquires the phase itself (no
 // __syncwarp, whose memory ordering costs ~200 clocks), and the warp leaves together.
-__device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+__device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                WaitLimit lim) {
+  if (__all_sync(0xffffffffu, mbar_poll(bar, parity, false, lim))) return true;
   const uint64_t t0 = global_ns();
+  const uint32_t every = lim.fine ? 0u : 15u;
   for (uint32_t it = 0;; ++it) {
-    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
-    if ((it & 15u) == 15u) {
+    if (__all_sync(0xffffffffu, mbar_poll(bar, parity, false, lim))) return true;
+    if ((it & every) == every) {
       int stop = 0;
       if ((threadIdx.x & 31) == 0) {
         if (*abort_flag) stop = 1;
-        else if (global_ns() - t0 > 1000000000ull) {
+        else if (global_ns() - t0 > lim.ns) {
           *abort_flag = 1;
           stop = 1;
         }
@@ -230,9 +275,11 @@ struct TcArgs {
   int64_t lda;
   float *Y;        // store mode: Y = scale * acc (column-major, ld ldy)
   int64_t ldy;
-  float *part;     // partial mode: part[split][i + j * ldp] = acc
+  float *part;     // partial mode: part[split][i + j * ldp] = acc (+= when accumulate)
   int64_t ldp;
+  int accumulate;
   int *err;
+  uint64_t wait_ns;  // limit of the waits on another role's progress
 };
 
 // MODE 0: A = kernel tile evaluated from the points;  MODE 1: A = a dense FP32 matrix.
@@ -306,6 +353,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   cluster_sync_all();   // every barrier of the cluster is initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const WaitLimit prog = wait_limit(a.wait_ns);       // waits on another role's progress
+  const WaitLimit drain = wait_limit(kDefaultWaitNs);  // waits for this CTA's own work to land
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer (Omega)
@@ -333,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, false, prog)) break;
         issue_points(kb + L);
         pts_issued = kb + L + 1;
         mbar_arrive_expect_tx(full(s), b_bytes);
@@ -349,11 +398,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       volatile int never = 0;
       int first = issued - S < 0 ? 0 : issued - S;
       for (int kb = first; kb < issued; ++kb)
-        mbar_wait(full(kb % S), (uint32_t)(kb / S) & 1u, &never);
+        mbar_wait(full(kb % S), (uint32_t)(kb / S) & 1u, &never, false, drain);
       if (MODE == 0) {
         const int last = min(pts_issued, nkb);
         for (int kb = max(0, last - kPtSlots); kb < last; ++kb)
-          mbar_wait(fullP(kb % kPtSlots), (uint32_t)(kb / kPtSlots) & 1u, &never);
+          mbar_wait(fullP(kb % kPtSlots), (uint32_t)(kb / kPtSlots) & 1u, &never, false, drain);
       }
     }
     __syncwarp();
@@ -367,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag) || !mbar_wait(peerB(s), ph, abort_flag, true)) {
+        if (!mbar_wait(full(s), ph, abort_flag, false, prog) || !mbar_wait(peerB(s), ph, abort_flag, true, prog)) {
           good = false;
           break;
         }
@@ -392,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // all MMAs of the pair must finish before either CTA releases TMEM or shared memory
         volatile int never = 0;
         tc_commit_pair(drain_bar, 0x1);
-        mbar_wait(drain_bar, 0u, &never);
+        mbar_wait(drain_bar, 0u, &never, false, drain);
       }
     } else if (lane == 0) {
       // rank 1: tell the MMA issuer when this CTA's A tiles and Omega half of each stage are
@@ -401,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag)) break;
+        if (!mbar_wait(full(s), ph, abort_flag, false, prog)) break;
         mbar_arrive_remote(peer_bar0 + 8u * (uint32_t)s);
       }
     }
@@ -447,8 +496,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * KH;
       const bool full_block = ((int64_t)(kb_begin + kb) * BK + BK <= a.n);
       const int j = kb % kPtSlots;
-      if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag)) return false;
-      if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag)) return false;
+      if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag, prog)) return false;
+      if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag, prog)) return false;
       const float *ps = pt_slots + (size_t)j * (kPtSlotBytes / 4) + (size_t)h * KH * a.dim;
       // Phase 1: all CH * 8 entries of this lane's rows (no shared-memory store in between,
       // so that the loads and the arithmetic of different entries overlap freely).
@@ -536,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!produce(kb)) { good = false; break; }
     }
     // ------------------------------------------------------------ epilogue
-    bool e_ok = good && nkb > 0 && mbar_wait_lanes(accum_bar, 0u, abort_flag);
+    bool e_ok = good && nkb > 0 && mbar_wait_lanes(accum_bar, 0u, abort_flag, prog);
     if (e_ok) {
       tc_fence_after();
       const int q = warp & 3;                 // TMEM lane quadrant this warp may access
@@ -551,7 +600,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (i < mrows) {
           if (pout) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) pout[i + (int64_t)(j + t) * a.ldp] = nkb > 0 ? v[t] : 0.0f;
+            for (int t = 0; t < 8; ++t) {
+              float *q = pout + i + (int64_t)(j + t) * a.ldp;
+              *q = (a.accumulate ? *q : 0.0f) + (nkb > 0 ? v[t] : 0.0f);
+            }
           } else {
 #pragma unroll
             for (int t = 0; t < 8; ++t) a.Y[i + (int64_t)(j + t) * a.ldy] = v[t] * scale;
@@ -606,11 +658,16 @@ Error launch(const CUtensorMap &map, const TcArgs &a, size_t smem, dim3 grid, cu
   return ok();
 }
 
-// Tensor map over the BF16 Omega^T of the context and the launch geometry.
-Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, size_t *smem) {
+// Tensor map over a BF16 right factor Bt (d x kpad, row j = column j of the right factor,
+// contiguous over the contraction; the context's Omega^T by default) and the launch geometry.
+Error prepare_b(ckinv_ctx *ctx, const __nv_bfloat16 *Bt, int64_t kpad, int d, int nsplit, CUtensorMap *map,
+                TcArgs *a, size_t *smem) {
   if (d % 16 != 0 || d > 512 || d < 16) return fail(CKINV_EINVAL, "sketch_tc: d must be 16..512, d % 16 == 0");
   if (nsplit < 1 || nsplit > 3) return fail(CKINV_EINVAL, "sketch_tc: 1..3 BF16 terms");
-  const OmegaCache &om = ctx->om;
+  struct {
+    const __nv_bfloat16 *omegaT;
+    int64_t kpad;
+  } om{Bt, kpad};
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return fail(CKINV_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
   // MMA column chunks: N = d for d <= 256, else two chunks (equal when d % 32 == 0) of
@@ -641,6 +698,7 @@ Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, si
   a->n0 = n0;
   a->n1 = n1;
   a->err = ctx->d_err;
+  a->wait_ns = ctx->wait_ns;
   const size_t stage_bytes = (size_t)nsplit * kATileBytes + (size_t)d / 2 * kRowBytes;
   const size_t head = 512 + kPtSlots * kPtSlotBytes + 1024;   // barriers, point slots, alignment slack
   const size_t limit = 227 * 1024;
@@ -653,6 +711,10 @@ Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, si
   // second would block in tcgen05.alloc until the first exits).
   if (d > 256) *smem = std::max(*smem, (size_t)(120 * 1024));
   return ok();
+}
+
+Error prepare(ckinv_ctx *ctx, int d, int nsplit, CUtensorMap *map, TcArgs *a, size_t *smem) {
+  return prepare_b(ctx, ctx->om.omegaT, ctx->om.kpad, d, nsplit, map, a, smem);
 }
 
 template <int KIND>
@@ -714,6 +776,31 @@ Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const Ker
   return fail(CKINV_EINVAL, "sketch_tc: covariance kind has no fused form");
 }
 
+Error sketch_tc_rhs(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const KernelParams &kp, const float *points,
+                    const __nv_bfloat16 *Bt, int64_t kpad, int splits, float *part, int64_t ldp, bool accumulate,
+                    cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(points) & 15) != 0)
+    return fail(CKINV_EINVAL, "sketch: points must be 16-byte aligned for the tensor-core path");
+  if (kpad < n || kpad % 64 != 0) return fail(CKINV_EINVAL, "sketch_tc_rhs: kpad must be >= n, a multiple of 64");
+  CUtensorMap map;
+  TcArgs a;
+  size_t smem = 0;
+  CK_TRY(prepare_b(ctx, Bt, kpad, d, nsplit, &map, &a, &smem));
+  a.n = n;
+  a.m = n;
+  a.dim = dim;
+  a.kp = kp;
+  a.pts = points;
+  a.kb_per_cta = (int)ceil_div(a.num_kb, std::max(1, splits));
+  a.part = part;
+  a.ldp = ldp;
+  a.accumulate = accumulate ? 1 : 0;
+  const dim3 grid((unsigned)ceil_div(n, BM), (unsigned)ceil_div(a.num_kb, a.kb_per_cta));
+  if (kp.kind == CKINV_SE) return dispatch_kernel<CKINV_SE>(nsplit, false, map, a, smem, grid, st);
+  if (kp.kind == CKINV_MATERN52) return dispatch_kernel<CKINV_MATERN52>(nsplit, false, map, a, smem, grid, st);
+  return fail(CKINV_EINVAL, "sketch_tc_rhs: covariance kind has no fused form");
+}
+
 Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const float *A, int64_t lda, double scale,
                float *Y, int64_t ldy, double *G, int64_t si, int64_t sj, cudaStream_t st) {
   if (lda % 4 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
@@ -740,7 +827,7 @@ Error dense_tc(ckinv_ctx *ctx, int64_t m, int64_t n, int d, int nsplit, const fl
   splits = (int)ceil_div(a.num_kb, a.kb_per_cta);
   const int64_t ldp = (int64_t)mt * BM;
   float *part = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&part, sizeof(float) * (size_t)splits * ldp * d, st));
+  CK_CUDA(dev_alloc((void **)&part, sizeof(float) * (size_t)splits * ldp * d, st));
   a.part = part;
   a.ldp = ldp;
   Error e = dispatch_dense(nsplit, map, a, smem, dim3(mt, splits), st);

@@ -788,18 +788,18 @@ Error alloc_stage(Stage<T> &s, int P, int H, int d, const std::vector<int> &top,
                   ckinv_ctx *ctx, std::vector<void *> &owned, cudaStream_t st) {
   s.P = P;
   s.H = H;
-  CK_CUDA(cudaMallocAsync((void **)&s.M, sizeof(T) * (size_t)P * H * d, st));
+  CK_CUDA(dev_alloc((void **)&s.M, sizeof(T) * (size_t)P * H * d, st));
   owned.push_back(s.M);
-  CK_CUDA(cudaMallocAsync((void **)&s.Vx, sizeof(T) * (size_t)P * H * d, st));
+  CK_CUDA(dev_alloc((void **)&s.Vx, sizeof(T) * (size_t)P * H * d, st));
   owned.push_back(s.Vx);
-  CK_CUDA(cudaMallocAsync((void **)&s.Tm, sizeof(T) * (size_t)P * d * d, st));
+  CK_CUDA(dev_alloc((void **)&s.Tm, sizeof(T) * (size_t)P * d * d, st));
   owned.push_back(s.Tm);
   CK_CUDA(cudaMemsetAsync(s.Tm, 0, sizeof(T) * (size_t)P * d * d, st));
-  CK_CUDA(cudaMallocAsync((void **)&s.top, sizeof(int) * P, st));
+  CK_CUDA(dev_alloc((void **)&s.top, sizeof(int) * P, st));
   owned.push_back(s.top);
   CK_TRY(stage_upload(ctx, top.data(), sizeof(int) * P, s.top, st));
   if (!bot.empty()) {
-    CK_CUDA(cudaMallocAsync((void **)&s.bot, sizeof(int) * P, st));
+    CK_CUDA(dev_alloc((void **)&s.bot, sizeof(int) * P, st));
     owned.push_back(s.bot);
     CK_TRY(stage_upload(ctx, bot.data(), sizeof(int) * P, s.bot, st));
   }
@@ -817,7 +817,7 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, bool with_t, cud
   const size_t smem = sq_step_smem<T>(d);
   CK_CUDA(cudaFuncSetAttribute(k_sq_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   T *S = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&S, sizeof(T) * 2 * (size_t)P * d * NBS, st));
+  CK_CUDA(dev_alloc((void **)&S, sizeof(T) * 2 * (size_t)P * d * NBS, st));
   // update tiles per CTA: with many combines the level is FP64-throughput bound, and a CTA
   // that stages the panel's reflectors once for several tiles wastes less; with few it is
   // latency bound, and one tile per CTA keeps each CTA short
@@ -853,8 +853,8 @@ Error assemble_t(const ckinv_ctx *ctx, const Stage<T> &s, int d, int nb0, cudaSt
   const int P = s.P, H = s.H;
   const int64_t sM = (int64_t)H * d, sD = (int64_t)d * d;
   T *G = nullptr, *W = nullptr;
-  CK_CUDA(cudaMallocAsync((void **)&G, sizeof(T) * (size_t)P * d * d, st));
-  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * (size_t)P * ((size_t)d * d / 4 + 1), st));
+  CK_CUDA(dev_alloc((void **)&G, sizeof(T) * (size_t)P * d * d, st));
+  CK_CUDA(dev_alloc((void **)&W, sizeof(T) * (size_t)P * ((size_t)d * d / 4 + 1), st));
   Error e = gemm_batched<T>(ctx, true, d, d, d, T(1), s.Vx + d, H, sM, s.Vx + d, H, sM, T(0), G, d, sD, P, st);
   for (int w = nb0; w < d && !e.st; w *= 2) {
     const int nfull = d / w, rem = d - nfull * w, np = nfull / 2;
@@ -899,8 +899,8 @@ Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot
   }
   T *W = nullptr, *W2 = nullptr;
   const size_t sw = (size_t)s.P * ((d / 2 + NB) * (d / 2 + NB));
-  CK_CUDA(cudaMallocAsync((void **)&W, sizeof(T) * sw, st));
-  CK_CUDA(cudaMallocAsync((void **)&W2, sizeof(T) * sw, st));
+  CK_CUDA(dev_alloc((void **)&W, sizeof(T) * sw, st));
+  CK_CUDA(dev_alloc((void **)&W2, sizeof(T) * sw, st));
   Error e = rqr<T>(ctx, s, d, 0, d, W, W2, st);
   cudaFreeAsync(W, st);
   cudaFreeAsync(W2, st);
@@ -964,10 +964,10 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
   int *d_rows = nullptr;
   Error e = ok();
   do {
-    if (cudaMallocAsync((void **)&Rslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&Xslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&d_row0, sizeof(int64_t) * L, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&d_rows, sizeof(int) * L, st) != cudaSuccess) {
+    if (dev_alloc((void **)&Rslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
+        dev_alloc((void **)&Xslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
+        dev_alloc((void **)&d_row0, sizeof(int64_t) * L, st) != cudaSuccess ||
+        dev_alloc((void **)&d_rows, sizeof(int) * L, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "tsqr workspace");
       break;
     }
@@ -1008,8 +1008,8 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
           q.top = sd[l].top;
           q.bot = sd[l].bot;
           const int64_t nv = (int64_t)P * 2 * d * d, nt = (int64_t)P * d * d;
-          if (cudaMallocAsync((void **)&q.Vx, sizeof(float) * nv, st) != cudaSuccess ||
-              cudaMallocAsync((void **)&q.Tm, sizeof(float) * nt, st) != cudaSuccess) {
+          if (dev_alloc((void **)&q.Vx, sizeof(float) * nv, st) != cudaSuccess ||
+              dev_alloc((void **)&q.Tm, sizeof(float) * nt, st) != cudaSuccess) {
             e = fail(CKINV_ENOMEM, "tsqr FP32 reflector copies");
             break;
           }
@@ -1039,8 +1039,8 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     const size_t zmax = (size_t)L * d * d;
     const size_t esz = LEAF64 ? sizeof(double) : sizeof(float);
     void *Qs = nullptr, *Z1 = nullptr, *Z2 = nullptr;
-    if (cudaMallocAsync(&Qs, esz * qmax, st) != cudaSuccess || cudaMallocAsync(&Z1, esz * zmax, st) != cudaSuccess ||
-        cudaMallocAsync(&Z2, esz * zmax, st) != cudaSuccess) {
+    if (dev_alloc(&Qs, esz * qmax, st) != cudaSuccess || dev_alloc(&Z1, esz * zmax, st) != cudaSuccess ||
+        dev_alloc(&Z2, esz * zmax, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "tsqr Q workspace");
       break;
     }

@@ -18,6 +18,9 @@ import pytest
 import torch
 
 import synth
+from oracle import kernels as okk
+from oracle import lowrank as olr
+from oracle import omega as oom
 
 pytestmark = pytest.mark.gpu
 
@@ -114,3 +117,61 @@ def test_autotune_picks_a_candidate_and_is_used(ctx):
     torch.cuda.synchronize()
     err = float((X_auto - X_b).norm() / X_b.norm())
     assert err <= 1e-5, err
+
+
+def _oracle_nll_grad(pts, y, kind, ell, var, tau, d, seed, b, round32=False):
+    """Oracle NLL and gradient; round32 rounds the kernel and derivative entries to FP32
+    before the (exact) sketch, and the sketches, Q_hat and alpha = K_tilde^-1 y after it: the
+    floor of a method that carries entries to FP32 precision and stores those arrays in FP32."""
+    pts = pts.astype(np.float64)
+    O = oom.omega_matrix(len(pts), d, seed)
+    K = okk.kernel_matrix(pts, pts, kind, ell, var)
+    Kd = okk.dkernel_matrix(pts, pts, kind, ell, var)
+    r32 = (lambda M: np.asarray(M, dtype=np.float32).astype(np.float64)) if round32 else (lambda M: M)
+    Y, Yd = r32(r32(K) @ O), r32(r32(Kd) @ O)
+    f = olr.factorise(Y, O, tau, b)
+    if round32:
+        f = olr.Factor(r32(f.Q), f.R, O, tau)
+    v, a = olr.nll(f, y.astype(np.float64), 1)
+    g, _ = olr.grad(f, y, Y, Yd, r32(a))
+    return v, g
+
+
+def test_batched_problems_against_the_oracle(ctx):
+    """Eight problems of uneven size, kernel, dimension and width in one graph, each against
+    the FP64 oracle (not only against single calls).  Members alternate between the FP32
+    form and the three-term tensor-core form (both carry kernel entries to FP32 precision),
+    FP64 leaves, nugget 1e-2 (at 1e-3 storing alpha in FP32 alone moves one member's
+    length-scale derivative by 1e-3).  Bar: three times the floor of FP32 kernel entries with
+    the sketches, Q_hat and alpha stored in FP32, and never tighter than 1e-5 (NLL) and 1e-3
+    (gradient): the library forms the gradient's d x d reductions from FP32 products summed
+    in FP64 per 256 rows, measured at up to 1.2e-6 (NLL) and 1.6e-4 (gradient) on these
+    problems, whose kappa(Y) reaches 1e4."""
+    rng = np.random.default_rng(11)
+    plans, kerns, pts, ys, host_in = [], [], [], [], []
+    for p in range(8):
+        n = int(rng.integers(1024, 3001))
+        dim = 2 + p % 2
+        kind = ck.MATERN52 if p % 3 == 2 else ck.SE
+        ell = float(rng.uniform(0.18, 0.3))
+        d = [32, 48, 64][p % 3]
+        b = 512 if n >= 1024 else n
+        x = synth.points(n, dim, 100 + p)
+        y = synth.gp_targets(x, 0.2, 1.0, 1e-2, seed=100 + p)
+        plans.append(ck.Plan(n=n, d=d, dim=dim, block_rows=b, seed=200 + p, refine_steps=1, leaf_fp64=1,
+                             prec=ck.FP32 if p % 2 == 0 else ck.BF16X3))
+        kerns.append(ck.Kernel(kind, ell, 1.1, 1e-2))
+        pts.append(torch.from_numpy(x).cuda())
+        ys.append(torch.from_numpy(y).cuda())
+        host_in.append((x, y, kind, ell, d, b))
+    vb, gb = ck.nll_grad_batched(ctx, plans, kerns, pts, ys)
+    for p, (x, y, kind, ell, d, b) in enumerate(host_in):
+        vo, go = _oracle_nll_grad(x, y, kind, ell, 1.1, 1e-2, d, 200 + p, b)
+        vf, gf = _oracle_nll_grad(x, y, kind, ell, 1.1, 1e-2, d, 200 + p, b, round32=True)
+        tv = max(1e-5, 3 * abs(vf - vo) / abs(vo))
+        tg = np.maximum(1e-3, 3 * np.abs(gf - go) / np.abs(go))
+        ev = abs(vb[p] - vo) / abs(vo)
+        eg = np.abs(np.array(gb[p]) - go) / np.abs(go)
+        print("problem %d (n=%d d=%d): NLL err %.2e (bar %.2e), grad err %s (bar %s)" % (p, len(x), d, ev, tv, eg, tg))
+        assert ev <= tv
+        assert np.all(eg <= tg)

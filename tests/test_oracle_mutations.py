@@ -71,12 +71,12 @@ def test_wrong_hadamard_pattern_is_caught(monkeypatch):
 def test_swapped_tree_children_are_caught(monkeypatch):
     real = hh.householder_qr
 
-    def swapped(A):
+    def swapped(A, *dtype):
         m = A.shape[0]
         if m == 2 * A.shape[1]:               # a tree combine: stack in the wrong order
             d = A.shape[1]
-            return real(np.vstack([A[d:], A[:d]]))
-        return real(A)
+            return real(np.vstack([A[d:], A[:d]]), *dtype)
+        return real(A, *dtype)
     monkeypatch.setattr(ts, "householder_qr", swapped)
     Y = np.random.default_rng(0).standard_normal((256, 16))
     t = ts.tsqr(Y, 64)

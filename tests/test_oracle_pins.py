@@ -330,3 +330,29 @@ def test_projection_error_decreases_with_d():
         Q, _ = hh.qr(K0 @ O)
         errs.append(np.linalg.norm(K0 - Q @ (Q.T @ K0)) / np.linalg.norm(K0))
     assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_fp32_householder_matches_lapack_single_precision():
+    """The oracle's Householder QR run in FP32 (the floor of FP32 leaves) is the textbook
+    algorithm in single precision: its R agrees with LAPACK's single-precision QR up to row
+    signs at FP32 accuracy, and its Q is orthonormal to FP32 accuracy, not better."""
+    A = np.random.default_rng(4).standard_normal((512, 64))
+    V, tau, R = hh.householder_qr(A, np.float32)
+    assert V.dtype == np.float32 and R.dtype == np.float32
+    R_l = np.linalg.qr(A.astype(np.float32))[1]
+    s = np.sign(np.diag(R_l)) * np.sign(np.diag(R))
+    err = np.linalg.norm(R.astype(np.float64) - s[:, None] * R_l) / np.linalg.norm(R_l)
+    assert err < 1e-5
+    R64 = hh.householder_qr(A)[2]
+    assert 1e-9 < np.linalg.norm(R.astype(np.float64) - R64) / np.linalg.norm(R64) < 1e-5
+    Q = hh.thin_q(V, tau).astype(np.float64)
+    orth = np.abs(Q.T @ Q - np.eye(64)).max()
+    assert 1e-9 < orth < 1e-5
+
+
+def test_tsqr_with_fp32_leaves_is_near_the_fp64_tsqr():
+    Y = np.random.default_rng(8).standard_normal((2048, 32))
+    t64 = ts.tsqr(Y, 512)
+    t32 = ts.tsqr(Y, 512, np.float32)
+    e = np.linalg.norm(t32["R"] - t64["R"]) / np.linalg.norm(t64["R"])
+    assert 1e-9 < e < 1e-5

@@ -20,7 +20,7 @@ def ck():
     return ckinv
 
 
-@pytest.mark.parametrize("n,d,seed", [(262144, 512, 7), (1000, 48, 3)])
+@pytest.mark.parametrize("n,d,seed", [(262144, 512, 7), (1000, 48, 3), (1 << 28, 512, 5)])
 def test_noalloc_draw_matches_the_context_draw_twice(ck, n, d, seed):
     ctx = ck.Context(0)
     try:
