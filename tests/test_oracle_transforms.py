@@ -135,3 +135,52 @@ def test_kronecker_split_of_the_walsh_hadamard_product(A, B):
     U = v.reshape(A, B) @ HB.T                         # row k_a: the B-point transform of block k_a
     split = (HA.T @ U).reshape(N)                      # output p = p_a * B + p_b
     assert np.allclose(split, dense, atol=1e-12 * np.abs(v).sum())
+
+
+def test_two_pass_core_equals_dense_projection_and_solves():
+    """S = Q^T K0 Q against the dense product; the Woodbury solve and log-determinant against
+    LAPACK on the dense tau I + Q S Q^T; exact recovery of (K0 + tau I)^-1 A when
+    rank(K0) <= d (the projection then loses nothing)."""
+    from oracle import householder as hh
+    from oracle import kernels as kk
+    from oracle import omega as om
+    from oracle import projection as pr
+    n, d, tau = 300, 24, 1e-3
+    pts = np.random.default_rng(2).random((n, 2))
+    K = kk.kernel_matrix(pts, pts, kk.SE, 0.2, 1.3)
+    Q, _ = hh.qr(K @ om.omega_matrix(n, d, 5))
+    S = pr.two_pass_core(pts, kk.SE, 0.2, 1.3, Q, col_block=64)
+    assert np.allclose(S, Q.T @ K @ Q, rtol=0, atol=1e-12 * np.abs(S).max())
+    assert np.allclose(S, S.T, atol=1e-12 * np.abs(S).max())
+    assert np.linalg.eigvalsh(S).min() > -1e-12 * np.abs(S).max()
+    A = np.random.default_rng(3).standard_normal((n, 3))
+    Kt = tau * np.eye(n) + Q @ S @ Q.T
+    X = pr.two_pass_solve(Q, S, tau, A)
+    assert np.linalg.norm(X - np.linalg.solve(Kt, A)) <= 1e-9 * np.linalg.norm(X)
+    assert abs(pr.two_pass_logdet(S, tau, n) - np.linalg.slogdet(Kt)[1]) <= 1e-9 * abs(np.linalg.slogdet(Kt)[1])
+    # exact rank r <= d: K0 = E D E^T, the two-pass solve is the dense solve of K0 + tau I
+    E, _ = np.linalg.qr(np.random.default_rng(4).standard_normal((n, d)))
+    K0 = E @ np.diag(np.exp(-0.3 * np.arange(d))) @ E.T
+    Q2, _ = hh.qr(K0 @ om.omega_matrix(n, d, 6))
+    S2 = Q2.T @ K0 @ Q2
+    X2 = pr.two_pass_solve(Q2, S2, tau, A)
+    Xd = np.linalg.solve(K0 + tau * np.eye(n), A)
+    assert np.linalg.norm(X2 - Xd) <= 1e-8 * np.linalg.norm(Xd)
+
+
+def test_two_pass_with_transposed_product_is_caught():
+    """A slip that uses S Q^T A's transpose order (Q^T A S) breaks the dense check."""
+    from oracle import householder as hh
+    from oracle import kernels as kk
+    from oracle import omega as om
+    from oracle import projection as pr
+    n, d, tau = 200, 16, 1e-2
+    pts = np.random.default_rng(7).random((n, 2))
+    K = kk.kernel_matrix(pts, pts, kk.SE, 0.25, 1.0)
+    Q, _ = hh.qr(K @ om.omega_matrix(n, d, 1))
+    S = Q.T @ K @ Q
+    A = np.random.default_rng(8).standard_normal((n, d))
+    V = np.linalg.solve(tau * np.eye(d) + S, (Q.T @ A) @ S)
+    bad = (A - Q @ V) / tau
+    good = pr.two_pass_solve(Q, S, tau, A)
+    assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
