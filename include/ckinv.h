@@ -210,6 +210,85 @@ ckinv_status ckinv_factor_q(const ckinv_factor *f, float *Q, int64_t ldq,
 ckinv_status ckinv_factor_core(const ckinv_factor *f, double *B, double *Cp,
                                double *logdet, ckinv_stream stream);
 
+/* ---------------------------------------------------------------- row shards (several GPUs)
+ * The paper's tree of QRs runs across "units" (Sec. 3.3: the blocks of Eq. 1 are factored
+ * in parallel, then pairs of R factors are combined, Eqs. 2-3).  Across GPUs the rows of Y
+ * are split into G contiguous shards, one per GPU; the points and Omega's seed are on every
+ * GPU.  One solve takes these calls, with the collectives between them made by the caller
+ * (for example over NCCL; no call here communicates):
+ *   1. ckinv_sketch_rows      this shard's rows of Y (the contraction runs over all n points)
+ *   2. ckinv_tsqr_shard       local TSQR: a shard factor and its d x d R  -> all-gather the R's
+ *   3. ckinv_shard_combine    the top of the tree over the G R's (redundantly on every GPU),
+ *                             the shard's rows of Q_hat, and its part of B  -> all-reduce B
+ *   4. ckinv_shard_core       C' = R^T + tau B and the LUs (redundantly)
+ *   5. ckinv_shard_solve_begin  Q_hat_shard^T A_shard                  -> all-reduce Z
+ *   6. ckinv_shard_solve_end    the shard's rows of X = K_tilde^-1 A
+ * The shard factor's solve takes no refinement step.  R, B and X equal those of one GPU
+ * holding all rows up to rounding (the tree's pairing differs unless every shard holds the
+ * same power-of-two number of leaves; R and Q_hat are unique for a full-rank Y). */
+
+/* Rows row0 .. row0 + m - 1 of Y = K0 Omega (as ckinv_sketch, which is row0 = 0, m = n):
+ * points (all n, as in ckinv_sketch), or the columns row0 .. row0 + m - 1 of a materialised
+ * K (= its rows, K being symmetric).  Y: m x d FP32 column-major, ldy >= m. */
+ckinv_status ckinv_sketch_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                               const ckinv_kernel *kern, const float *points, const float *K,
+                               int64_t ldk, int64_t row0, int64_t m, float *Y, int64_t ldy,
+                               ckinv_stream stream);
+
+/* Local TSQR of a shard's m rows of Y (rows row0 .. row0 + m - 1 of the problem that
+ * plan->n describes; d <= m).  *out receives a shard factor (free with ckinv_factor_free);
+ * R_local (device, d x d FP64, ld = d) receives the shard's R (diag >= 0). */
+ckinv_status ckinv_tsqr_shard(ckinv_ctx *ctx, const ckinv_plan_desc *plan,
+                              const ckinv_kernel *kern, float *Y, int64_t ldy, int64_t row0,
+                              int64_t m, ckinv_factor **out, double *R_local, ckinv_stream stream);
+
+/* Top of the tree over the G shards' R factors (R_all: device, G blocks of d x d FP64, block
+ * k = shard k's R), combined pairwise in FP64 as Eqs. 2-3; the shard factor's R becomes the
+ * root R and its Q_hat the shard's rows of the whole Q_hat.  B_partial (device d x d FP64)
+ * receives Omega[rows of this shard]^T Q_hat_shard, whose sum over the shards is B. */
+ckinv_status ckinv_shard_combine(ckinv_ctx *ctx, ckinv_factor *f, const double *R_all, int32_t G,
+                                 int32_t g, double *B_partial, ckinv_stream stream);
+
+/* B (device d x d FP64, the sum of the shards' B_partial): C' = R^T + tau B and the FP64 LUs
+ * of B and C' in the shard factor. */
+ckinv_status ckinv_shard_core(ckinv_ctx *ctx, ckinv_factor *f, const double *B, ckinv_stream stream);
+
+/* Z_partial (device d x m FP64, ld = d) = Q_hat_shard^T A_shard; A_shard: the shard's m_rows x m
+ * rows of A (FP32, lda >= the shard's rows).  The sum over the shards is Q_hat^T A. */
+ckinv_status ckinv_shard_solve_begin(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda,
+                                     int32_t m, double *Z_partial, ckinv_stream stream);
+
+/* The shard's rows of X = tau^-1 (A - Q_hat C'^-1 R^T Z), Z = Q_hat^T A (device d x m FP64,
+ * the sum of the shards' Z_partial).  X may equal A. */
+ckinv_status ckinv_shard_solve_end(ckinv_ctx *ctx, const ckinv_factor *f, const double *Z, const float *A,
+                                   int64_t lda, int32_t m, float *X, int64_t ldx, ckinv_stream stream);
+
+/* Second pass over K0 (the projection Q Q^T K of the proof of Theorem 3, made symmetric):
+ * S = Q_hat^T K0 Q_hat (d x d FP64), computed matrix-free from the points on the tensor
+ * cores (Q_hat split into three BF16 terms, kernel entries into three, the products of order
+ * at most two, partial sums over 4096-point ranges folded in FP64).  Afterwards the factor's
+ * core is the two-pass one: ckinv_solve applies K_tilde = tau I + Q_hat S Q_hat^T, solved
+ * through the FP64 LU of S + tau I (no inverse of Omega^T Y, and positive semi-definite).
+ *   plan, kern, points: as given to ckinv_sketch for this factor (plan->n and d must match).
+ *   S: device d x d (ld = d) copy of S, or NULL.
+ *   colspace_err: host; if not NULL receives ||K0 - Q Q^T K0||_F / ||K0||_F, the paper's
+ *     accuracy measure (Sec. 3.1, Theorem 3), evaluated as sqrt(1 - ||K0 Q||^2 / ||K0||^2)
+ *     with ||K0||_F^2 from FP64 kernel entries (n^2 of them; errors below ~1e-3 are not
+ *     resolved by that difference); the call then synchronises `stream`.
+ * Must run on the stream the factor was created on. */
+ckinv_status ckinv_factor_project(ckinv_ctx *ctx, ckinv_factor *f, const ckinv_plan_desc *plan,
+                                  const ckinv_kernel *kern, const float *points, double *S,
+                                  double *colspace_err, ckinv_stream stream);
+
+/* Gaussian-process predictive mean at n_new points (the prediction task of Sec. 5's data
+ * example): mean[i] = sum_k K0(x*_i, x_k) alpha_k, alpha = K_tilde^-1 y as ckinv_solve gives
+ * it.  Kernel entries and sums in FP64 (alpha's terms reach |y| / tau and cancel).
+ *   points: n x dim FP32 (the plan's), alpha: n FP32, new_points: n_new x dim FP32 row-major,
+ *   mean: n_new FP64, all device. */
+ckinv_status ckinv_predict_mean(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern,
+                                const float *points, const float *alpha, const float *new_points,
+                                int64_t n_new, double *mean, ckinv_stream stream);
+
 /* X = K_tilde^-1 A (Sec. 1's R^-1 Q^T A in Woodbury form), then plan->refine_steps
  * steps of FP64 iterative refinement X += K_tilde^-1 (A - K_tilde X).
  *   A: n x m FP32 (lda >= n);  X: n x m FP32 (ldx >= n); X may equal A.  1 <= m <= 256.

@@ -66,6 +66,19 @@ _SIGS = {
     "ckinv_factor_r": (ctypes.c_int, [_VP, _VP, _VP]),
     "ckinv_factor_q": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     "ckinv_factor_core": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+    "ckinv_sketch_rows": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "ckinv_tsqr_shard": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_VP), _VP, _VP]),
+    "ckinv_shard_combine": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    "ckinv_shard_core": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ckinv_shard_solve_begin": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
+    "ckinv_shard_solve_end": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, ctypes.c_int64,
+                                             _VP]),
+    "ckinv_factor_project": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
+                                            ctypes.POINTER(ctypes.c_double), _VP]),
+    "ckinv_predict_mean": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP, _VP,
+                                          ctypes.c_int64, _VP, _VP]),
     "ckinv_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, ctypes.c_int64, _VP]),
     "ckinv_kinv_a": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                     ctypes.c_int64, ctypes.c_int32, _VP, ctypes.c_int64, _VP]),
@@ -285,6 +298,92 @@ class Factor:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- row shards
+def sketch_rows(ctx, plan, kern, row0, m, points=None, K=None, Y=None, stream=None):
+    """Rows row0 .. row0 + m - 1 of Y = K0 Omega (column-major m x d float32)."""
+    if Y is None:
+        Y = colmajor(m, plan.d)
+    ldy = _colmajor_ld(Y, m)
+    ldk = _colmajor_ld(K, plan.n) if K is not None else 0
+    pd, kd = plan.desc(), kern.desc()
+    ctx._raise(load().ckinv_sketch_rows(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(points), _ptr(K), ldk,
+                                        row0, m, _ptr(Y), ldy, _stream(stream)))
+    return Y
+
+
+def tsqr_shard(ctx, plan, kern, Y, row0, stream=None):
+    """Local TSQR of a row shard: (shard Factor, its d x d R as a float64 tensor, column-major
+    storage: R_storage[j, i] = R[i, j])."""
+    m = Y.shape[0]
+    ldy = _colmajor_ld(Y, m)
+    R = torch.empty((plan.d, plan.d), dtype=torch.float64, device="cuda")
+    h = ctypes.c_void_p()
+    pd, kd = plan.desc(), kern.desc()
+    ctx._raise(load().ckinv_tsqr_shard(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(Y), ldy, row0, m,
+                                       ctypes.byref(h), _ptr(R), _stream(stream)))
+    f = Factor(ctx, h, Plan(n=m, d=plan.d, dim=plan.dim))
+    return f, R
+
+
+def shard_combine(ctx, factor, R_all, G, g, stream=None):
+    """R_all: (G, d, d) float64 device tensor of the shards' R storages.  Returns this shard's
+    B_partial storage (d, d) float64."""
+    d = factor.plan.d
+    Bp = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    ctx._raise(load().ckinv_shard_combine(ctx.handle, factor.handle, _ptr(R_all.contiguous()), G, g, _ptr(Bp),
+                                          _stream(stream)))
+    return Bp
+
+
+def shard_core(ctx, factor, B, stream=None):
+    ctx._raise(load().ckinv_shard_core(ctx.handle, factor.handle, _ptr(B.contiguous()), _stream(stream)))
+
+
+def shard_solve_begin(ctx, factor, A, stream=None):
+    """Z_partial = Q_hat_shard^T A_shard as a (m, d) float64 storage (column-major d x m)."""
+    rows = factor.plan.n
+    m = 1 if A.dim() == 1 else A.shape[1]
+    lda = _colmajor_ld(A, rows)
+    Z = torch.empty((m, factor.plan.d), dtype=torch.float64, device="cuda")
+    ctx._raise(load().ckinv_shard_solve_begin(ctx.handle, factor.handle, _ptr(A), lda, m, _ptr(Z), _stream(stream)))
+    return Z
+
+
+def shard_solve_end(ctx, factor, Z, A, X=None, stream=None):
+    rows = factor.plan.n
+    m = 1 if A.dim() == 1 else A.shape[1]
+    lda = _colmajor_ld(A, rows)
+    if X is None:
+        X = colmajor(rows, m) if A.dim() == 2 else torch.empty_like(A)
+    ldx = _colmajor_ld(X, rows)
+    ctx._raise(load().ckinv_shard_solve_end(ctx.handle, factor.handle, _ptr(Z.contiguous()), _ptr(A), lda, m, _ptr(X),
+                                            ldx, _stream(stream)))
+    return X
+
+
+def project(ctx, factor, plan, kern, points, stream=None, colspace=True):
+    """Second pass: S = Q_hat^T K0 Q_hat; the factor's solves use the two-pass core afterwards.
+    Returns (S as a (d, d) float64 tensor, column-space error or None)."""
+    d = plan.d
+    S = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    err = ctypes.c_double()
+    pd, kd = plan.desc(), kern.desc()
+    ctx._raise(load().ckinv_factor_project(ctx.handle, factor.handle, ctypes.byref(pd), ctypes.byref(kd),
+                                           _ptr(points), _ptr(S), ctypes.byref(err) if colspace else None,
+                                           _stream(stream)))
+    return S.t(), (err.value if colspace else None)
+
+
+def predict_mean(ctx, plan, kern, points, alpha, new_points, stream=None):
+    """mu* = K0(X*, X) alpha at the rows of new_points (float64 tensor)."""
+    n_new = new_points.shape[0]
+    mean = torch.empty((n_new,), dtype=torch.float64, device="cuda")
+    pd, kd = plan.desc(), kern.desc()
+    ctx._raise(load().ckinv_predict_mean(ctx.handle, ctypes.byref(pd), ctypes.byref(kd), _ptr(points), _ptr(alpha),
+                                         _ptr(new_points), n_new, _ptr(mean), _stream(stream)))
+    return mean
 
 
 def tsqr(ctx, plan, kern, Y, stream=None):

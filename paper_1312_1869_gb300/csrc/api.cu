@@ -195,6 +195,12 @@ __global__ void k_check_finite(const float *x, int64_t rows, int64_t cols, int64
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, DERR_NONFINITE);
 }
 
+// dst = (float) src, n elements.
+__global__ void k_narrow_f64(const double *src, int64_t n, float *dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
 Error check_finite(ckinv_ctx *ctx, const float *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return ok();
   const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows * cols, 256), (int64_t)ctx->sm_count * 4);
@@ -204,10 +210,14 @@ Error check_finite(ckinv_ctx *ctx, const float *x, int64_t rows, int64_t cols, i
   return ok();
 }
 
+// Rows row0 .. row0 + m - 1 of the sketch (m < 0: all n rows).
 Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
-                const float *K, int64_t ldk, bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+                const float *K, int64_t ldk, bool deriv, float *Y, int64_t ldy, cudaStream_t st, int64_t row0 = 0,
+                int64_t m = -1) {
   CK_TRY(check_plan(plan, kern, true));
-  if (!Y || ldy < plan->n) return fail(CKINV_EINVAL, "Y must be non-null with ldy >= n");
+  if (m < 0) m = plan->n;
+  if (row0 < 0 || m < 1 || row0 + m > plan->n) return fail(CKINV_EINVAL, "rows must lie in [0, n)");
+  if (!Y || ldy < m) return fail(CKINV_EINVAL, "Y must be non-null with ldy >= its row count");
   if (kern->kind == CKINV_DENSE) {
     if (!K || ldk < plan->n) return fail(CKINV_EINVAL, "dense kernel needs K with ldk >= n");
     if (deriv) return fail(CKINV_EINVAL, "no derivative sketch for a materialised K");
@@ -220,12 +230,12 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
   if (kern->kind == CKINV_DENSE) {
     // K is symmetric: its column i is read as row i (16-byte rows for the tensor-core path)
     if (plan->prec != CKINV_FP32 && ldk % 4 == 0 && (reinterpret_cast<uintptr_t>(K) & 15) == 0)
-      return dense_tc(ctx, plan->n, plan->n, plan->d, plan->prec, K, ldk, kp.scale, Y, ldy, nullptr, 0, 0, st);
-    return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, nullptr, K, ldk, false, Y, ldy, st);
+      return dense_tc(ctx, m, plan->n, plan->d, plan->prec, K + row0 * ldk, ldk, kp.scale, Y, ldy, nullptr, 0, 0, st);
+    return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, nullptr, K, ldk, false, Y, ldy, st, row0, m);
   }
   if (plan->prec == CKINV_FP32)
-    return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, points, nullptr, 0, deriv, Y, ldy, st);
-  return sketch_tc(ctx, plan->n, plan->dim, plan->d, plan->prec, kp, points, deriv, Y, ldy, st);
+    return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, points, nullptr, 0, deriv, Y, ldy, st, row0, m);
+  return sketch_tc(ctx, plan->n, plan->dim, plan->d, plan->prec, kp, points, deriv, Y, ldy, st, row0, m);
 }
 
 void factor_release(ckinv_factor *f) {
@@ -587,12 +597,84 @@ Error do_nll_grad(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kerne
 // ------------------------------------------------------------------ batched likelihood
 // Every problem gets a context of its own (its Omega buffers are reserved here, so nothing
 // allocates through the context during capture); the problems' pipelines are captured on
-// kBatchStreams forked streams of one CUDA graph, which is instantiated and launched once.
+// kBatchStreams forked streams of one CUDA graph, which is instantiated and launched.  The
+// instantiated graph is kept on the calling context with everything it refers to (the
+// per-problem contexts, the pinned upload arena, the output buffer): a later call with the
+// same problems - the same descriptors and the same input pointers - launches it again
+// without capturing or instantiating anything.
 constexpr int kBatchStreams = 8;
+
+}  // namespace
+
+struct ckinv_batch_graph {
+  std::vector<unsigned char> key;            // descriptors and pointers of the captured batch
+  std::vector<ckinv_ctx *> sub;
+  ckinv::UploadArena arena;
+  double *d_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nprob = 0;
+};
+
+namespace {
+
+void batch_graph_release(ckinv_batch_graph *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (ckinv_ctx *c : b->sub) {
+    if (!c) continue;
+    for (void *q : {(void *)c->d_err, (void *)c->hist, (void *)c->cand, (void *)c->cand_idx, (void *)c->small,
+                    (void *)c->om.bits, (void *)c->om.cols, (void *)c->om.omegaT})
+      if (q) cudaFree(q);
+    delete c;
+  }
+  if (b->arena.host) cudaFreeHost(b->arena.host);
+  if (b->d_out) cudaFree(b->d_out);
+  delete b;
+}
+
+std::vector<unsigned char> batch_key(int nprob, const ckinv_plan_desc *plans, const ckinv_kernel *kerns,
+                                     const float *const *points, const float *const *y) {
+  std::vector<unsigned char> k;
+  auto put = [&](const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    k.insert(k.end(), c, c + n);
+  };
+  put(&nprob, sizeof(nprob));
+  put(plans, sizeof(ckinv_plan_desc) * nprob);
+  put(kerns, sizeof(ckinv_kernel) * nprob);
+  put(points, sizeof(const float *) * nprob);
+  put(y, sizeof(const float *) * nprob);
+  return k;
+}
+
+// Launch a captured batch and read its results and the problems' device errors.
+Error batch_graph_run(ckinv_batch_graph *b, cudaStream_t st, double *nll, double *grad) {
+  std::vector<double> hout((size_t)b->nprob * 4, 0.0);
+  ::ckinv::note_launch();
+  cudaError_t ce;
+  if ((ce = cudaGraphLaunch(b->exec, st)) != cudaSuccess ||
+      (ce = cudaMemcpyAsync(hout.data(), b->d_out, sizeof(double) * 4 * b->nprob, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (ce = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(CKINV_ECUDA, std::string("batched graph: ") + cudaGetErrorString(ce));
+  for (int p = 0; p < b->nprob; ++p) {
+    Error pe = read_device_error(b->sub[p], st);
+    if (pe.st) return fail(pe.st, "problem " + std::to_string(p) + ": " + pe.msg);
+  }
+  for (int p = 0; p < b->nprob; ++p) {
+    nll[p] = hout[4 * p];
+    for (int k = 0; k < 3; ++k) grad[3 * p + k] = hout[4 * p + 1 + k];
+  }
+  return ok();
+}
 
 Error do_nll_grad_batched(ckinv_ctx *ctx, int nprob, const ckinv_plan_desc *plans, const ckinv_kernel *kerns,
                           const float *const *points, const float *const *y, double *nll, double *grad,
                           cudaStream_t st) {
+  std::vector<unsigned char> key = batch_key(nprob, plans, kerns, points, y);
+  if (ctx->batch && ctx->batch->key == key) return batch_graph_run(ctx->batch, st, nll, grad);
   std::vector<ckinv_plan_desc> pl(plans, plans + nprob);
   for (int p = 0; p < nprob; ++p) {
     CK_TRY(check_plan(&pl[p], &kerns[p], true));
@@ -611,34 +693,39 @@ Error do_nll_grad_batched(ckinv_ctx *ctx, int nprob, const ckinv_plan_desc *plan
     if (!known) CK_TRY(autotune_leaf_rows(ctx, &pl[p], st, &b));
     pl[p].block_rows = leaf_rows(ctx, &pl[p]);
   }
-  std::vector<ckinv_ctx *> sub(nprob, nullptr);
-  UploadArena arena;
-  double *d_out = nullptr;
+  // a new batch replaces the kept one
+  if (ctx->batch) {
+    cudaStreamSynchronize(st);
+    batch_graph_release(ctx->batch);
+    ctx->batch = nullptr;
+  }
+  ckinv_batch_graph *bg = new ckinv_batch_graph();
+  bg->key = key;
+  bg->nprob = nprob;
+  bg->sub.assign(nprob, nullptr);
   const int ns = std::min(nprob, kBatchStreams);
   std::vector<cudaStream_t> ws(ns, nullptr);
   std::vector<cudaEvent_t> join(ns, nullptr);
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;   // the capture origin (the caller's stream may be the legacy one)
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  std::vector<double> hout((size_t)nprob * 4, 0.0);
   Error e = ok();
   do {
     for (int p = 0; p < nprob && !e.st; ++p) {
-      sub[p] = new ckinv_ctx();
-      sub[p]->device = ctx->device;
-      sub[p]->sm_count = ctx->sm_count;
-      if (cudaMalloc((void **)&sub[p]->d_err, sizeof(int)) != cudaSuccess ||
-          cudaMemsetAsync(sub[p]->d_err, 0, sizeof(int), st) != cudaSuccess) {
+      bg->sub[p] = new ckinv_ctx();
+      bg->sub[p]->device = ctx->device;
+      bg->sub[p]->sm_count = ctx->sm_count;
+      bg->sub[p]->wait_ns = ctx->wait_ns;
+      if (cudaMalloc((void **)&bg->sub[p]->d_err, sizeof(int)) != cudaSuccess ||
+          cudaMemsetAsync(bg->sub[p]->d_err, 0, sizeof(int), st) != cudaSuccess) {
         e = fail(CKINV_ENOMEM, "batch context");
         break;
       }
-      e = omega_reserve(sub[p], pl[p].n, pl[p].d, st);
+      e = omega_reserve(bg->sub[p], pl[p].n, pl[p].d, st);
     }
     if (e.st) break;
-    arena.cap = ((size_t)1 << 20) + (size_t)nprob * (256 << 10);
-    if (cudaMallocHost((void **)&arena.host, arena.cap) != cudaSuccess ||
-        cudaMalloc((void **)&d_out, sizeof(double) * 4 * nprob) != cudaSuccess) {
+    bg->arena.cap = ((size_t)1 << 20) + (size_t)nprob * (256 << 10);
+    if (cudaMallocHost((void **)&bg->arena.host, bg->arena.cap) != cudaSuccess ||
+        cudaMalloc((void **)&bg->d_out, sizeof(double) * 4 * nprob) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "batch buffers");
       break;
     }
@@ -663,39 +750,26 @@ Error do_nll_grad_batched(ckinv_ctx *ctx, int nprob, const ckinv_plan_desc *plan
     cudaEventRecord(fork, cap);
     for (int w = 0; w < ns; ++w) cudaStreamWaitEvent(ws[w], fork, 0);
     for (int p = 0; p < nprob && !e.st; ++p) {
-      sub[p]->capture_arena = &arena;
-      e = nll_grad_enqueue(sub[p], &pl[p], &kerns[p], points[p], y[p], d_out + 4 * p, ws[p % ns]);
-      sub[p]->capture_arena = nullptr;
+      bg->sub[p]->capture_arena = &bg->arena;
+      e = nll_grad_enqueue(bg->sub[p], &pl[p], &kerns[p], points[p], y[p], bg->d_out + 4 * p, ws[p % ns]);
+      bg->sub[p]->capture_arena = nullptr;
     }
     for (int w = 0; w < ns; ++w) {
       cudaEventRecord(join[w], ws[w]);
       cudaStreamWaitEvent(cap, join[w], 0);
     }
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    cudaError_t ce = cudaStreamEndCapture(cap, &bg->graph);
     if (e.st) break;
-    if (ce != cudaSuccess || !graph) {
+    if (ce != cudaSuccess || !bg->graph) {
       e = fail(CKINV_ECUDA, std::string("graph capture of the batch failed: ") + cudaGetErrorString(ce));
       break;
     }
-    if ((ce = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+    if ((ce = cudaGraphInstantiate(&bg->exec, bg->graph, 0)) != cudaSuccess) {
       e = fail(CKINV_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ce));
       break;
     }
-    ::ckinv::note_launch();
-    if ((ce = cudaGraphLaunch(exec, st)) != cudaSuccess ||
-        (ce = cudaMemcpyAsync(hout.data(), d_out, sizeof(double) * 4 * nprob, cudaMemcpyDeviceToHost, st)) !=
-            cudaSuccess ||
-        (ce = cudaStreamSynchronize(st)) != cudaSuccess) {
-      e = fail(CKINV_ECUDA, std::string("batched graph: ") + cudaGetErrorString(ce));
-      break;
-    }
-    for (int p = 0; p < nprob && !e.st; ++p) {
-      Error pe = read_device_error(sub[p], st);
-      if (pe.st) e = fail(pe.st, "problem " + std::to_string(p) + ": " + pe.msg);
-    }
+    e = batch_graph_run(bg, st, nll, grad);
   } while (0);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
   cudaStreamSynchronize(st);
   for (int w = 0; w < ns; ++w) {
     if (ws[w]) cudaStreamDestroy(ws[w]);
@@ -703,22 +777,12 @@ Error do_nll_grad_batched(ckinv_ctx *ctx, int nprob, const ckinv_plan_desc *plan
   }
   if (fork) cudaEventDestroy(fork);
   if (cap) cudaStreamDestroy(cap);
-  for (ckinv_ctx *c : sub) {
-    if (!c) continue;
-    for (void *q : {(void *)c->d_err, (void *)c->hist, (void *)c->cand, (void *)c->cand_idx, (void *)c->small,
-                    (void *)c->om.bits, (void *)c->om.cols, (void *)c->om.omegaT})
-      if (q) cudaFree(q);
-    delete c;
+  if (e.st) {
+    batch_graph_release(bg);
+    return e;
   }
-  if (arena.host) cudaFreeHost(arena.host);
-  if (d_out) cudaFree(d_out);
-  if (e.st == CKINV_OK) {
-    for (int p = 0; p < nprob; ++p) {
-      nll[p] = hout[4 * p];
-      for (int k = 0; k < 3; ++k) grad[3 * p + k] = hout[4 * p + 1 + k];
-    }
-  }
-  return e;
+  ctx->batch = bg;
+  return ok();
 }
 
 }  // namespace
@@ -773,6 +837,7 @@ ckinv_status ckinv_destroy(ckinv_ctx *ctx) {
   for (void *p : {(void *)ctx->d_err, (void *)ctx->hist, (void *)ctx->cand, (void *)ctx->cand_idx,
                   (void *)ctx->small, (void *)ctx->om.bits, (void *)ctx->om.cols, (void *)ctx->om.omegaT})
     if (p) cudaFree(p);
+  batch_graph_release(ctx->batch);
   if (ctx->device < kPoolDevices) {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     if (--g_live_ctx[ctx->device] == 0 && g_pool[ctx->device]) cudaMemPoolTrimTo(g_pool[ctx->device], 0);
@@ -896,6 +961,150 @@ ckinv_status ckinv_factor_core(const ckinv_factor *f, double *B, double *Cp, dou
     *logdet = (double)(f->n - f->d) * std::log(f->tau) + lp[1] - lp[0];
   }
   return CKINV_OK;
+}
+
+// ------------------------------------------------------------------ row shards
+ckinv_status ckinv_sketch_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern,
+                               const float *points, const float *K, int64_t ldk, int64_t row0, int64_t m, float *Y,
+                               int64_t ldy, ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  DeviceGuard g(ctx->device);
+  return finish(ctx, do_sketch(ctx, plan, kern, points, K, ldk, false, Y, ldy, (cudaStream_t)stream, row0, m));
+}
+
+ckinv_status ckinv_tsqr_shard(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, float *Y,
+                              int64_t ldy, int64_t row0, int64_t m, ckinv_factor **out, double *R_local,
+                              ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Error e = check_plan(plan, kern, false);
+  if (e.st == CKINV_OK && (!Y || !out || !R_local || row0 < 0 || m < plan->d || row0 + m > plan->n || ldy < m))
+    e = fail(CKINV_EINVAL, "need Y, out, R_local, 0 <= row0, d <= m, row0 + m <= n, ldy >= m");
+  if (e.st) return finish(ctx, e);
+  *out = nullptr;
+  const int d = plan->d;
+  ckinv_plan_desc local = *plan;
+  local.n = m;
+  int b = leaf_rows(ctx, &local);
+  e = omega_draw(ctx, plan->n, d, plan->seed, st);
+  if (e.st) return finish(ctx, e);
+  ckinv_factor *f = new ckinv_factor();
+  f->ctx = ctx;
+  f->device = ctx->device;
+  f->stream = st;
+  f->n = m;
+  f->d = d;
+  f->tau = kern->nugget;
+  f->refine_steps = 0;
+  f->prec = plan->prec;
+  f->omega_scale = 1.0 / std::sqrt((double)padded_order(plan->n));
+  f->row0 = row0;
+  f->n_total = plan->n;
+  auto alloc = [&](void **p, size_t bytes) {
+    if (e.st != CKINV_OK) return;
+    cudaError_t ce = dev_alloc(p, bytes, st);
+    if (ce != cudaSuccess) e = fail(CKINV_ENOMEM, std::string("factor allocation: ") + cudaGetErrorString(ce));
+  };
+  const size_t dd = (size_t)d * d;
+  alloc((void **)&f->Q, sizeof(float) * (size_t)m * d);
+  alloc((void **)&f->R, sizeof(double) * dd);
+  alloc((void **)&f->B, sizeof(double) * dd);
+  alloc((void **)&f->Cp, sizeof(double) * dd);
+  alloc((void **)&f->luB, sizeof(double) * dd * 2);
+  alloc((void **)&f->pivB, sizeof(int32_t) * d * 2);
+  if (e.st == CKINV_OK) {
+    f->luC = f->luB + dd;
+    f->pivC = f->pivB + d;
+  }
+  alloc((void **)&f->logdet_parts, sizeof(double) * 2);
+  alloc((void **)&f->bits, sizeof(uint32_t) * ceil_div(plan->n, 32));
+  alloc((void **)&f->cols, sizeof(int32_t) * d);
+  if (e.st == CKINV_OK &&
+      (cudaMemcpyAsync(f->bits, ctx->om.bits, sizeof(uint32_t) * ceil_div(plan->n, 32), cudaMemcpyDeviceToDevice, st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(f->cols, ctx->om.cols, sizeof(int32_t) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+    e = fail(CKINV_ECUDA, "copy of Omega into the factor failed");
+  if (e.st == CKINV_OK)
+    e = tsqr_factor(ctx, m, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, tsqr_on_tensor_cores(plan), Y, ldy,
+                    f->Q, f->R, st);
+  if (e.st == CKINV_OK && cudaMemcpyAsync(R_local, f->R, sizeof(double) * dd, cudaMemcpyDeviceToDevice, st) !=
+                              cudaSuccess)
+    e = fail(CKINV_ECUDA, "copy of R failed");
+  if (e.st != CKINV_OK) {
+    factor_release(f);
+    return finish(ctx, e);
+  }
+  *out = f;
+  return CKINV_OK;
+}
+
+ckinv_status ckinv_shard_combine(ckinv_ctx *ctx, ckinv_factor *f, const double *R_all, int32_t G, int32_t g,
+                                 double *B_partial, ckinv_stream stream) {
+  if (!ctx || !f) return finish(ctx, fail(CKINV_EINVAL, "null context or factor"));
+  if (!R_all || !B_partial || G < 1 || g < 0 || g >= G || f->n_total == 0)
+    return finish(ctx, fail(CKINV_EINVAL, "need a shard factor, R_all, B_partial and 0 <= g < G"));
+  DeviceGuard gd(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = f->d;
+  const size_t dd = (size_t)d * d;
+  double *X = nullptr;
+  float *X32 = nullptr, *Qn = nullptr;
+  Error e = ok();
+  do {
+    if (dev_alloc(&X, sizeof(double) * G * dd, st) != cudaSuccess || dev_alloc(&X32, sizeof(float) * dd, st) != cudaSuccess ||
+        dev_alloc(&Qn, sizeof(float) * (size_t)f->n * d, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "shard combine workspace");
+      break;
+    }
+    // the top of the tree over all shards' R factors (every rank computes it redundantly)
+    if ((e = tsqr_combine_r(ctx, G, d, R_all, f->R, X, st)).st) break;
+    note_launch();
+    k_narrow_f64<<<64, 256, 0, st>>>(X + (size_t)g * dd, (int64_t)dd, X32);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+      e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
+      break;
+    }
+    // this shard's rows of Q_hat: its own Q_hat times its block of the top Q factor
+    if ((e = gemm_batched<float>(ctx, false, (int)f->n, d, d, 1.0f, f->Q, f->n, 0, X32, d, 0, 0.0f, Qn, f->n, 0, 1,
+                                 st)).st)
+      break;
+    std::swap(f->Q, Qn);
+    // B_partial = Omega[row0 : row0 + n_local]^T Q_hat_local
+    e = tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, B_partial, st, f->row0);
+  } while (0);
+  for (void *p : {(void *)X, (void *)X32, (void *)Qn})
+    if (p) cudaFreeAsync(p, st);
+  return finish(ctx, e);
+}
+
+ckinv_status ckinv_shard_core(ckinv_ctx *ctx, ckinv_factor *f, const double *B, ckinv_stream stream) {
+  if (!ctx || !f || !B) return finish(ctx, fail(CKINV_EINVAL, "null argument"));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(f->B, B, sizeof(double) * f->d * f->d, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return finish(ctx, fail(CKINV_ECUDA, "copy of B failed"));
+  return finish(ctx, core_from_b(ctx, f, st));
+}
+
+ckinv_status ckinv_shard_solve_begin(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda, int32_t m,
+                                     double *Z_partial, ckinv_stream stream) {
+  if (!ctx || !f || !A || !Z_partial || lda < f->n || m < 1 || m > 256)
+    return finish(ctx, fail(CKINV_EINVAL, "need A, Z_partial, lda >= rows, 1 <= m <= 256"));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Error e = check_finite(ctx, A, f->n, m, lda, st);
+  if (e.st == CKINV_OK) e = tsprod(ctx, f->n, f->d, m, f->Q, f->n, nullptr, nullptr, 0.0, A, lda, Z_partial, st);
+  return finish(ctx, e);
+}
+
+ckinv_status ckinv_shard_solve_end(ckinv_ctx *ctx, const ckinv_factor *f, const double *Z, const float *A, int64_t lda,
+                                   int32_t m, float *X, int64_t ldx, ckinv_stream stream) {
+  if (!ctx || !f || !Z || !A || !X || lda < f->n || ldx < f->n || m < 1 || m > 256)
+    return finish(ctx, fail(CKINV_EINVAL, "need Z, A, X, lda/ldx >= rows, 1 <= m <= 256"));
+  DeviceGuard g(ctx->device);
+  return finish(ctx, solve_from_z(ctx, f, Z, A, lda, m, X, ldx, (cudaStream_t)stream));
 }
 
 ckinv_status ckinv_factor_project(ckinv_ctx *ctx, ckinv_factor *f, const ckinv_plan_desc *plan,

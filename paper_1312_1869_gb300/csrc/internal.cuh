@@ -91,6 +91,8 @@ struct UploadArena {
 
 }  // namespace ckinv
 
+struct ckinv_batch_graph;
+
 struct ckinv_ctx {
   // pinned host staging ring for small descriptor uploads (no host synchronisation)
   struct Stage {
@@ -112,6 +114,8 @@ struct ckinv_ctx {
   size_t cand_cap = 0;
   // set while the context's work is being captured into a CUDA graph
   ckinv::UploadArena *capture_arena = nullptr;
+  // the last batched likelihood's instantiated CUDA graph and what it refers to
+  struct ckinv_batch_graph *batch = nullptr;
   // FP32 GEMMs on the tensor cores (split BF16) rather than the CUDA cores; set by
   // tsqr_factor for the duration of one factorization
   bool gemm_tc = false;
@@ -145,6 +149,10 @@ struct ckinv_factor {
   double *S2 = nullptr;      // d x d S, then d x d packed LU of S + tau I
   int32_t *pivS = nullptr;
   double *logdet2 = nullptr; // ln|det(S + tau I)|
+  // row shard (ckinv_tsqr_shard): this factor holds rows row0 .. row0 + n - 1 of a problem of
+  // n_total points; Omega's signs and columns are those of the whole problem
+  int64_t row0 = 0;
+  int64_t n_total = 0;
 };
 
 namespace ckinv {
@@ -179,16 +187,18 @@ Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st);   // ctx->om.omeg
 Error omega_reserve(ckinv_ctx *ctx, int64_t n, int32_t d, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- sketch
+// Rows row0 .. row0 + m - 1 of Y = K0 Omega (m < 0: all n rows); with a materialised K its
+// rows (columns, K being symmetric) row0 .. row0 + m - 1 are read.
 Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp,
                   const float *points, const float *K, int64_t ldk, bool deriv,
-                  float *Y, int64_t ldy, cudaStream_t st);
+                  float *Y, int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
 // K (n x n FP32, column-major, ld ldk) = var * rho(x_i, x_k), each entry evaluated in FP64
 // from the FP32 points and rounded once.
 Error kernel_matrix(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, float *K,
                     int64_t ldk, cudaStream_t st);
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
-                int64_t ldy, cudaStream_t st);
+                int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
 // Tensor-core contraction of a dense FP32 matrix with Omega (the context's current draw):
 // rows i < m of A (row i at A + i*lda, contiguous over the n-long contraction), split into
 // nsplit BF16 terms.  Either Y (column-major, store) = scale * A Omega, or
@@ -204,6 +214,9 @@ struct TsqrOut {
 Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
                   const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
 int auto_block_rows(int64_t n, int d, int sm_count);
+// Tree combine of G given R factors (FP64, strided d x d): root R (diag >= 0) and each leaf's
+// d x d block of the combined Q factor.
+Error tsqr_combine_r(ckinv_ctx *ctx, int G, int d, const double *Rin, double *Rout, double *Xout, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- GEMM
 // C_b = alpha op(A_b) B_b + beta C_b for b < batch (column-major, strided batches).
@@ -226,12 +239,17 @@ Error gemm_batched2(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T al
 // L == nullptr, Omega generated from bits/cols/scale.
 Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl,
              const uint32_t *bits, const int32_t *cols, double oscale, const float *M,
-             int64_t ldm, double *G, cudaStream_t st);
+             int64_t ldm, double *G, cudaStream_t st, int64_t orow0 = 0);
 Error lu_factor_f64(ckinv_ctx *ctx, int n, double *A, int32_t *piv, double *logabsdet,
                     cudaStream_t st);
 Error lowrank_solve(ckinv_ctx *ctx, const ckinv_factor *f, const float *A, int64_t lda,
                     int m, float *X, int64_t ldx, int refine_steps, cudaStream_t st);
 Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st);
+// C' = R^T + tau B and the LUs of B and C' from the factor's R and B (B already in f->B).
+Error core_from_b(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st);
+// X = tau^-1 (A - Q_hat C'^-1 R^T Z) for a given Z = Q_hat^T A (row shards: Z all-reduced).
+Error solve_from_z(ckinv_ctx *ctx, const ckinv_factor *f, const double *Z, const float *A, int64_t lda, int m,
+                   float *X, int64_t ldx, cudaStream_t st);
 // Second pass over K0: S = Q_hat^T K0 Q_hat (tensor cores, Q_hat in three BF16 terms, partial
 // sums folded in FP64), the factor switched to the two-pass core, and (if colspace is not
 // null) the column-space error ||K0 - Q Q^T K0||_F / ||K0||_F written to host *colspace.

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
                                                 int64_t ldl, const uint32_t *__restrict__ bits,
                                                 const int32_t *__restrict__ cols, double oscale,
                                                 const float *__restrict__ M, int64_t ldm, double *G,
-                                                int64_t rows_per_split) {
+                                                int64_t rows_per_split, int64_t orow0) {
   static_assert((TM / 4) * (TN / 4) == 256, "4 x 4 outputs per thread");
   __shared__ float Ls[32][TM + 4];
   __shared__ float Ms[32][TN + 4];
@@ -49,8 +49,9 @@ __global__ void __launch_bounds__(256) k_tsprod(int64_t n, int d1, int d2, const
       float lv = 0.f;
       if (k < re && i0 + c < d1) {
         if (OMEGA) {
-          uint32_t s = (bits[k >> 5] >> (k & 31)) & 1u;
-          s ^= (uint32_t)(__popcll((unsigned long long)k & (unsigned long long)pc[c]) & 1);
+          const int64_t kg = orow0 + k;           // row of Omega (a row shard starts at orow0)
+          uint32_t s = (bits[kg >> 5] >> (kg & 31)) & 1u;
+          s ^= (uint32_t)(__popcll((unsigned long long)kg & (unsigned long long)pc[c]) & 1);
           lv = s ? -1.0f : 1.0f;
         } else {
           lv = L[k + (int64_t)(i0 + c) * ldl];
@@ -695,7 +696,8 @@ static Error fold_splits(int64_t count, int splits, double *part, double *G, cud
 }
 
 Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t ldl, const uint32_t *bits,
-             const int32_t *cols, double oscale, const float *M, int64_t ldm, double *G, cudaStream_t st) {
+             const int32_t *cols, double oscale, const float *M, int64_t ldm, double *G, cudaStream_t st,
+             int64_t orow0) {
   const bool narrow = d2 <= 32;                 // 128 x 32 tiles: no lanes wasted on a thin M
   const int TMv = narrow ? 128 : 64, TNv = narrow ? 32 : 64;
   int tx = (int)ceil_div(d1, TMv), ty = (int)ceil_div(d2, TNv);
@@ -707,11 +709,11 @@ Error tsprod(ckinv_ctx *ctx, int64_t n, int d1, int d2, const float *L, int64_t 
   dim3 grid(tx, ty, sp);
   ::ckinv::note_launch();
   if (narrow) {
-    if (L) k_tsprod<false, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
-    else k_tsprod<true, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+    if (L) k_tsprod<false, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps, orow0);
+    else k_tsprod<true, 128, 32><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps, orow0);
   } else {
-    if (L) k_tsprod<false, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
-    else k_tsprod<true, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps);
+    if (L) k_tsprod<false, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps, orow0);
+    else k_tsprod<true, 64, 64><<<grid, 256, 0, st>>>(n, d1, d2, L, ldl, bits, cols, oscale, M, ldm, part, rps, orow0);
   }
   CK_CUDA(cudaGetLastError());
   return fold_splits((int64_t)d1 * d2, sp, part, G, st);
@@ -796,10 +798,43 @@ Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
     CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
   else
     CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
+  return core_from_b(ctx, f, st);
+}
+
+Error core_from_b(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
+  const int d = f->d;
   ::ckinv::note_launch(), k_make_core<<<64, 256, 0, st>>>(d, f->R, f->B, f->tau, f->Cp, f->luB, f->luC);
   CK_CUDA(cudaGetLastError());
   // luB and luC (and pivB, pivC) are adjacent: one strided batch of two LUs
   CK_TRY(lu_blocked(ctx, 2, d, f->luB, f->pivB, f->logdet_parts, st));
+  return ok();
+}
+
+Error solve_from_z(ckinv_ctx *ctx, const ckinv_factor *f, const double *Z, const float *A, int64_t lda, int m,
+                   float *X, int64_t ldx, cudaStream_t st) {
+  (void)ctx;
+  const int d = f->d;
+  const int64_t n = f->n;
+  double *W = nullptr;
+  CK_CUDA(dev_alloc((void **)&W, sizeof(double) * d * m, st));
+  struct Release {
+    double *w;
+    cudaStream_t st;
+    ~Release() { cudaFreeAsync(w, st); }
+  } release{W, st};
+  dim3 g((unsigned)ceil_div(d, 128), (unsigned)m);
+  if (f->two_pass) {
+    ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->S2, Z, W, 0, 1.0);
+    CK_CUDA(cudaGetLastError());
+    CK_TRY(lu_solve(d, m, f->S2 + (size_t)d * d, f->pivS, W, 0, st));
+  } else {
+    ::ckinv::note_launch(), k_gemm_small<<<g, 128, 0, st>>>(d, m, f->R, Z, W, 1, 1.0);
+    CK_CUDA(cudaGetLastError());
+    CK_TRY(lu_solve(d, m, f->luC, f->pivC, W, 0, st));
+  }
+  dim3 gx((unsigned)ceil_div(n, 256), (unsigned)ceil_div(m, 32));
+  ::ckinv::note_launch(), k_apply_x<<<gx, 256, 0, st>>>(n, d, m, f->Q, n, W, A, lda, X, ldx, (float)(1.0 / f->tau));
+  CK_CUDA(cudaGetLastError());
   return ok();
 }
 

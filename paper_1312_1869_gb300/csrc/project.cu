@@ -60,23 +60,43 @@ __device__ __forceinline__ double rho_f64(int kind, double r2, double ell) {
   return (1.0 + u + u * u / 3.0) * exp(-u);
 }
 
-// Per-block partial sums of rho(x_i, x_k)^2 over all pairs (FP64 entries and sums); the
-// blocks' partials are folded in block order afterwards.
+// Per-block partial sums of rho(x_i, x_k)^2 over all pairs: one thread per row i, the points
+// x_k read by every lane of a warp at once (broadcast loads); entries in FP32 (expf, about one
+// unit of FP32 rounding), their squares summed in FP32 over 256 consecutive k and those
+// chunk sums added in FP64.  ||K0||_F^2 then carries ~1e-6 relative error, which resolves
+// column-space errors down to ~1e-3.
 constexpr int kSqThreads = 256;
-__global__ void __launch_bounds__(kSqThreads) k_kernel_sqnorm(int64_t n, int dim, int kind, double ell,
+__global__ void __launch_bounds__(kSqThreads) k_kernel_sqnorm(int64_t n, int dim, int kind, float ell,
                                                               const float *__restrict__ pts, double *partial) {
   __shared__ double red[kSqThreads];
   double acc = 0.0;
-  const int64_t total = n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, k = e % n;
-    double r2 = 0.0;
-    for (int t = 0; t < dim; ++t) {
-      const double df = (double)pts[i * dim + t] - (double)pts[k * dim + t];
-      r2 = fma(df, df, r2);
+  const float inv_l = 1.0f / ell;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool live = i < n;
+    float x[3] = {0.f, 0.f, 0.f};
+    if (live)
+      for (int t = 0; t < dim; ++t) x[t] = pts[i * dim + t];
+    for (int64_t k0 = 0; k0 < n; k0 += 256) {
+      const int64_t k1 = k0 + 256 < n ? k0 + 256 : n;
+      float chunk = 0.0f;
+      for (int64_t k = k0; k < k1; ++k) {
+        float r2 = 0.0f;
+        for (int t = 0; t < dim; ++t) {
+          const float df = x[t] - __ldg(pts + k * dim + t);
+          r2 = fmaf(df, df, r2);
+        }
+        float v;
+        if (kind == CKINV_SE) {
+          v = expf(-0.5f * r2 * inv_l * inv_l);
+        } else {
+          const float u = 2.2360679774997896f * sqrtf(r2) * inv_l;
+          v = (1.0f + u + u * u * (1.0f / 3.0f)) * expf(-u);
+        }
+        chunk = fmaf(v, v, chunk);
+      }
+      if (live) acc += (double)chunk;
     }
-    const double v = rho_f64(kind, r2, ell);
-    acc = fma(v, v, acc);
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -160,7 +180,7 @@ Error two_pass_core(ckinv_ctx *ctx, ckinv_factor *f, int dim, const KernelParams
   __nv_bfloat16 *Bt = nullptr;
   float *part = nullptr, *W = nullptr;
   double *norm_part = nullptr, *norms = nullptr;
-  const int sq_blocks = (int)std::min<int64_t>(ceil_div(n * n, kSqThreads), (int64_t)ctx->sm_count * 16);
+  const int sq_blocks = (int)ceil_div(n, kSqThreads);
   struct Release {
     std::vector<void *> p;
     cudaStream_t st;
@@ -208,7 +228,7 @@ Error two_pass_core(ckinv_ctx *ctx, ckinv_factor *f, int dim, const KernelParams
   if (colspace) {
     // ||K0 - Q Q^T K0||_F^2 = ||K0||_F^2 - ||K0 Q||_F^2 (Q orthonormal); ||K0||_F^2 in FP64
     note_launch();
-    k_kernel_sqnorm<<<sq_blocks, kSqThreads, 0, st>>>(n, dim, kp.kind, kp.ell, points, norm_part);
+    k_kernel_sqnorm<<<sq_blocks, kSqThreads, 0, st>>>(n, dim, kp.kind, (float)kp.ell, points, norm_part);
     note_launch();
     k_finish_norms<<<1, 1024, 0, st>>>(sq_blocks, norm_part, n * d, W, norms);
     CK_CUDA(cudaGetLastError());

@@ -120,32 +120,34 @@ __global__ void __launch_bounds__(256) k_contract(int64_t rows, int64_t kn, int 
 }  // namespace
 
 Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points,
-                  const float *K, int64_t ldk, bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+                  const float *K, int64_t ldk, bool deriv, float *Y, int64_t ldy, cudaStream_t st, int64_t row0,
+                  int64_t m) {
   const uint32_t *bits = ctx->om.bits;
   const int32_t *cols = ctx->om.cols;
   const double c = 1.0 / std::sqrt((double)padded_order(n));
+  if (m < 0) m = n;
   if (K) {
-    dim3 grid((unsigned)ceil_div(n, BM), (unsigned)ceil_div(d, BN));
-    ::ckinv::note_launch(), k_contract<<<grid, 256, 0, st>>>(n, n, d, K, ldk, bits, cols, c, Y, ldy);
+    dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(d, BN));
+    ::ckinv::note_launch(), k_contract<<<grid, 256, 0, st>>>(m, n, d, K + row0, ldk, bits, cols, c, Y, ldy);
     CK_CUDA(cudaGetLastError());
     return ok();
   }
   // row blocks of the kernel matrix, evaluated once each (about 2 GB of workspace at most)
   int64_t R = std::max<int64_t>(BM, ((int64_t)1 << 29) / std::max<int64_t>(n, 1));
-  R = std::min<int64_t>(R, n);
+  R = std::min<int64_t>(R, m);
   R = ceil_div(R, BM) * BM;
   float *Kb = nullptr;
   CK_CUDA(dev_alloc((void **)&Kb, sizeof(float) * R * n, st));
   const double ell = kp.ell, var = kp.var;
-  for (int64_t r0 = 0; r0 < n; r0 += R) {
-    int64_t rows = std::min<int64_t>(R, n - r0);
+  for (int64_t r0 = row0; r0 < row0 + m; r0 += R) {
+    int64_t rows = std::min<int64_t>(R, row0 + m - r0);
     unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows * n, 256), (int64_t)ctx->sm_count * 32);
     if (deriv)
       ::ckinv::note_launch(), k_kmat_f64<true><<<g, 256, 0, st>>>(rows, r0, n, dim, kp.kind, ell, var, points, Kb, rows);
     else
       ::ckinv::note_launch(), k_kmat_f64<false><<<g, 256, 0, st>>>(rows, r0, n, dim, kp.kind, ell, var, points, Kb, rows);
     dim3 grid((unsigned)ceil_div(rows, BM), (unsigned)ceil_div(d, BN));
-    ::ckinv::note_launch(), k_contract<<<grid, 256, 0, st>>>(rows, n, d, Kb, rows, bits, cols, c, Y + r0, ldy);
+    ::ckinv::note_launch(), k_contract<<<grid, 256, 0, st>>>(rows, n, d, Kb, rows, bits, cols, c, Y + (r0 - row0), ldy);
     CK_CUDA(cudaGetLastError());
   }
   CK_CUDA(cudaFreeAsync(Kb, st));

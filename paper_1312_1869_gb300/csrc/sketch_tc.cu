@@ -60,8 +60,7 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 }
 // try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
 // hint (ns) elapses, instead of spinning on the issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  const uint32_t hint_ns = 20000u;
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
@@ -72,8 +71,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // The same with cluster-scope acquire, for barriers that threads of the peer CTA arrive on.
-__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity) {
-  const uint32_t hint_ns = 20000u;
+__device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t ok;
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
@@ -83,57 +81,29 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint32_t bar, uint32_t parity) 
       : "memory");
   return ok != 0;
 }
-// Non-blocking polls (no suspension), for waits with a limit shorter than a suspend window.
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.b32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait_cl(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.b32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Limits of a wait: `ns` in all (the context's limit for waits on another role's progress,
-// the default second for waits on the CTA's own copies and MMAs to drain).  A limit of at
-// least 100 us polls with try_wait and a 20 us suspend hint, checking the clock every 16
-// polls; a shorter one polls with the non-blocking test_wait and checks the clock after
-// every poll, so that it runs out after about its own length.
-struct WaitLimit {
-  uint64_t ns;
-  bool fine;
-};
-__device__ __forceinline__ WaitLimit wait_limit(uint64_t ns) { return WaitLimit{ns, ns < 100000ull}; }
-__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity, bool cluster_scope, WaitLimit lim) {
-  if (lim.fine) return cluster_scope ? mbar_test_wait_cl(bar, parity) : mbar_test_wait(bar, parity);
-  return cluster_scope ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity);
-}
+// Limit of a wait, in ns: the context's limit for waits on another role's progress (a kernel
+// parameter, read where it is used so that the hot loops keep no register for it), the
+// default second for waits on the CTA's own copies and MMAs to drain.  Every poll suspends
+// for up to 20 us, or not at all under a limit below 100 us, whose loop then reads the clock
+// after every poll so that it runs out after about its own length.
+__device__ __forceinline__ uint32_t wait_hint(uint64_t limit_ns) { return limit_ns < 100000ull ? 0u : 20000u; }
 // Bounded wait: gives up after the limit or when another warp has flagged an abort.  The
 // first poll is inline; the loop is not.
 __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                            bool cluster_scope, WaitLimit lim) {
+                                            bool cluster_scope, uint64_t limit_ns) {
   const uint64_t t0 = global_ns();
-  const uint32_t every = lim.fine ? 0u : 15u;
+  const uint32_t hint = wait_hint(limit_ns);
+  const uint32_t every = hint ? 15u : 0u;
   for (uint32_t it = 0;; ++it) {
-    if (mbar_poll(bar, parity, cluster_scope, lim)) return true;
+    if (cluster_scope ? mbar_try_wait_cl(bar, parity, hint) : mbar_try_wait(bar, parity, hint)) return true;
     if ((it & every) == every) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > lim.ns) {
+      if (global_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         return false;
       }
@@ -141,25 +111,26 @@ __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volat
   }
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          bool cluster_scope, WaitLimit lim) {
-  if (mbar_poll(bar, parity, cluster_scope, lim)) return true;
-  return mbar_wait_slow(bar, parity, abort_flag, cluster_scope, lim);
+                                          bool cluster_scope, uint64_t limit_ns) {
+  const uint32_t hint = wait_hint(limit_ns);
+  if (cluster_scope ? mbar_try_wait_cl(bar, parity, hint) : mbar_try_wait(bar, parity, hint)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, cluster_scope, limit_ns);
 }
 
 // Warp-wide bounded wait: every lane polls, so that each lane acquires the phase itself (no
 // __syncwarp, whose memory ordering costs ~200 clocks), and the warp leaves together.
-__device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                                WaitLimit lim) {
-  if (__all_sync(0xffffffffu, mbar_poll(bar, parity, false, lim))) return true;
+__device__ __noinline__ bool mbar_wait_lanes_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                   uint64_t limit_ns) {
+  const uint32_t hint = wait_hint(limit_ns);
   const uint64_t t0 = global_ns();
-  const uint32_t every = lim.fine ? 0u : 15u;
+  const uint32_t every = hint ? 15u : 0u;
   for (uint32_t it = 0;; ++it) {
-    if (__all_sync(0xffffffffu, mbar_poll(bar, parity, false, lim))) return true;
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity, hint))) return true;
     if ((it & every) == every) {
       int stop = 0;
       if ((threadIdx.x & 31) == 0) {
         if (*abort_flag) stop = 1;
-        else if (global_ns() - t0 > lim.ns) {
+        else if (global_ns() - t0 > limit_ns) {
           *abort_flag = 1;
           stop = 1;
         }
@@ -167,6 +138,11 @@ __device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, v
       if (__shfl_sync(0xffffffffu, stop, 0)) return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait_lanes(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                uint64_t limit_ns) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity, wait_hint(limit_ns)))) return true;
+  return mbar_wait_lanes_slow(bar, parity, abort_flag, limit_ns);
 }
 // Contiguous bulk copy global -> shared (async proxy), completion counted on an mbarrier;
 // both addresses 16-byte aligned, bytes a multiple of 16.
@@ -260,8 +236,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
 }
 
 struct TcArgs {
-  int64_t n;       // contraction length (points); also the row count in kernel mode
-  int64_t m;       // output rows (dense mode: rows of A)
+  int64_t n;       // contraction length (points)
+  int64_t m;       // output rows (dense mode: rows of A; kernel mode: points row0 .. row0 + m - 1)
+  int64_t row0;    // kernel mode: first point of the output rows
   int dim;
   int d;
   int num_kb;      // BK-point blocks in total
@@ -353,8 +330,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   cluster_sync_all();   // every barrier of the cluster is initialised before any remote arrival
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const WaitLimit prog = wait_limit(a.wait_ns);       // waits on another role's progress
-  const WaitLimit drain = wait_limit(kDefaultWaitNs);  // waits for this CTA's own work to land
+  // limits: a.wait_ns for waits on another role's progress, kDefaultWaitNs for this CTA's
+  // own copies and MMAs to land
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer (Omega)
@@ -382,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, false, prog)) break;
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, false, a.wait_ns)) break;
         issue_points(kb + L);
         pts_issued = kb + L + 1;
         mbar_arrive_expect_tx(full(s), b_bytes);
@@ -398,11 +375,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       volatile int never = 0;
       int first = issued - S < 0 ? 0 : issued - S;
       for (int kb = first; kb < issued; ++kb)
-        mbar_wait(full(kb % S), (uint32_t)(kb / S) & 1u, &never, false, drain);
+        mbar_wait(full(kb % S), (uint32_t)(kb / S) & 1u, &never, false, kDefaultWaitNs);
       if (MODE == 0) {
         const int last = min(pts_issued, nkb);
         for (int kb = max(0, last - kPtSlots); kb < last; ++kb)
-          mbar_wait(fullP(kb % kPtSlots), (uint32_t)(kb / kPtSlots) & 1u, &never, false, drain);
+          mbar_wait(fullP(kb % kPtSlots), (uint32_t)(kb / kPtSlots) & 1u, &never, false, kDefaultWaitNs);
       }
     }
     __syncwarp();
@@ -416,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag, false, prog) || !mbar_wait(peerB(s), ph, abort_flag, true, prog)) {
+        if (!mbar_wait(full(s), ph, abort_flag, false, a.wait_ns) || !mbar_wait(peerB(s), ph, abort_flag, true, a.wait_ns)) {
           good = false;
           break;
         }
@@ -441,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // all MMAs of the pair must finish before either CTA releases TMEM or shared memory
         volatile int never = 0;
         tc_commit_pair(drain_bar, 0x1);
-        mbar_wait(drain_bar, 0u, &never, false, drain);
+        mbar_wait(drain_bar, 0u, &never, false, kDefaultWaitNs);
       }
     } else if (lane == 0) {
       // rank 1: tell the MMA issuer when this CTA's A tiles and Omega half of each stage are
@@ -450,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kb = 0; kb < nkb; ++kb) {
         int s = kb % S;
         uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(full(s), ph, abort_flag, false, prog)) break;
+        if (!mbar_wait(full(s), ph, abort_flag, false, a.wait_ns)) break;
         mbar_arrive_remote(peer_bar0 + 8u * (uint32_t)s);
       }
     }
@@ -467,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     static_assert(RG * KP == kProducerWarps && KH % 8 == 0 && KH <= 32, "producer layout");
     const int pw = warp - 2;
     const int g = pw % RG, h = pw / RG;
-    const int64_t rows_total = (MODE == 0) ? a.n : a.m;
+    const int64_t rows_total = a.m;
     const float cs = a.kp.coord_scale;
     const float inv_l = a.kp.inv_l;
     float xr[kRowsPerLane][3];
@@ -479,9 +456,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t irow = min(i0 + r, rows_total - 1);
       xr[j][0] = xr[j][1] = xr[j][2] = 0.f;
       if (MODE == 0) {
-        xr[j][0] = a.pts[irow * a.dim] * cs;
-        if (a.dim > 1) xr[j][1] = a.pts[irow * a.dim + 1] * cs;
-        if (a.dim > 2) xr[j][2] = a.pts[irow * a.dim + 2] * cs;
+        const int64_t ip = a.row0 + irow;
+        xr[j][0] = a.pts[ip * a.dim] * cs;
+        if (a.dim > 1) xr[j][1] = a.pts[ip * a.dim + 1] * cs;
+        if (a.dim > 2) xr[j][2] = a.pts[ip * a.dim + 2] * cs;
       }
       arow[j] = (MODE == 1) ? a.A + irow * a.lda : nullptr;
       rok[j] = (i0 + r < rows_total);
@@ -496,8 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * KH;
       const bool full_block = ((int64_t)(kb_begin + kb) * BK + BK <= a.n);
       const int j = kb % kPtSlots;
-      if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag, prog)) return false;
-      if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag, prog)) return false;
+      if (MODE == 0 && !mbar_wait_lanes(fullP(j), (uint32_t)(kb / kPtSlots) & 1u, abort_flag, a.wait_ns)) return false;
+      if (!mbar_wait_lanes(empty(s), ph ^ 1u, abort_flag, a.wait_ns)) return false;
       const float *ps = pt_slots + (size_t)j * (kPtSlotBytes / 4) + (size_t)h * KH * a.dim;
       // Phase 1: all CH * 8 entries of this lane's rows (no shared-memory store in between,
       // so that the loads and the arithmetic of different entries overlap freely).
@@ -585,14 +563,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!produce(kb)) { good = false; break; }
     }
     // ------------------------------------------------------------ epilogue
-    bool e_ok = good && nkb > 0 && mbar_wait_lanes(accum_bar, 0u, abort_flag, prog);
+    bool e_ok = good && nkb > 0 && mbar_wait_lanes(accum_bar, 0u, abort_flag, a.wait_ns);
     if (e_ok) {
       tc_fence_after();
       const int q = warp & 3;                 // TMEM lane quadrant this warp may access
       const int part = pw >> 2;               // kKParts warps per quadrant split the columns
       const int64_t i = i0 + q * 32 + lane;
       const float scale = (float)a.kp.scale;
-      const int64_t mrows = (MODE == 0) ? a.n : a.m;
+      const int64_t mrows = a.m;
       float *pout = a.part ? a.part + (int64_t)blockIdx.y * a.ldp * a.d : nullptr;
       for (int j = part * 8; j < a.d; j += 8 * kKParts) {
         float v[8];
@@ -755,7 +733,8 @@ __global__ void k_reduce_parts(int m, int d, int splits, const float *part, int6
 }  // namespace
 
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const KernelParams &kp, const float *points,
-                bool deriv, float *Y, int64_t ldy, cudaStream_t st) {
+                bool deriv, float *Y, int64_t ldy, cudaStream_t st, int64_t row0, int64_t m) {
+  if (m < 0) m = n;
   if ((reinterpret_cast<uintptr_t>(points) & 15) != 0)
     return fail(CKINV_EINVAL, "sketch: points must be 16-byte aligned for the tensor-core path");
   CK_TRY(omega_materialise_bf16(ctx, st));
@@ -764,13 +743,14 @@ Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit, const Ker
   size_t smem = 0;
   CK_TRY(prepare(ctx, d, nsplit, &map, &a, &smem));
   a.n = n;
-  a.m = n;
+  a.m = m;
+  a.row0 = row0;
   a.dim = dim;
   a.kp = kp;
   a.pts = points;
   a.Y = Y;
   a.ldy = ldy;
-  const dim3 grid((unsigned)ceil_div(n, BM), 1);
+  const dim3 grid((unsigned)ceil_div(m, BM), 1);
   if (kp.kind == CKINV_SE) return dispatch_kernel<CKINV_SE>(nsplit, deriv, map, a, smem, grid, st);
   if (kp.kind == CKINV_MATERN52) return dispatch_kernel<CKINV_MATERN52>(nsplit, deriv, map, a, smem, grid, st);
   return fail(CKINV_EINVAL, "sketch_tc: covariance kind has no fused form");

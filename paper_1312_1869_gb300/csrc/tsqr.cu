@@ -1109,4 +1109,87 @@ Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool
   return tsqr_impl<float>(ctx, n, d, b, fp64_levels, Y, ldy, Qout, Rout, st);
 }
 
+// The top of a TSQR whose leaves were factored elsewhere (row shards, one per GPU): the
+// binary tree of FP64 combines over the G given R factors (Rin, G strided d x d blocks,
+// column-major), the root normalised to diag(R) >= 0 (Rout), and every leaf's d x d block of
+// the combined Q factor (Xout, G strided blocks): the stacked R's equal Qtop Rout, so a
+// shard's final Q_hat rows are its own Q_hat times its block.  Pairs are formed left to
+// right and an odd node passes up, as in the single-GPU tree.
+Error tsqr_combine_r(ckinv_ctx *ctx, int G, int d, const double *Rin, double *Rout, double *Xout, cudaStream_t st) {
+  if (G < 1 || d % NB != 0) return fail(CKINV_EINVAL, "tsqr_combine_r: need G >= 1 and d % 16 == 0");
+  std::vector<Level> levels;
+  {
+    std::vector<int> active(G);
+    for (int i = 0; i < G; ++i) active[i] = i;
+    while (active.size() > 1) {
+      Level lv;
+      std::vector<int> nxt;
+      for (size_t i = 0; i + 1 < active.size(); i += 2) {
+        lv.top.push_back(active[i]);
+        lv.bot.push_back(active[i + 1]);
+        nxt.push_back(active[i]);
+      }
+      if (active.size() % 2) nxt.push_back(active.back());
+      active = nxt;
+      levels.push_back(lv);
+    }
+  }
+  const int Hn = (int)levels.size();
+  const size_t dd = (size_t)d * d;
+  std::vector<void *> owned;
+  double *Rslot = nullptr, *Xslot = nullptr;
+  Error e = ok();
+  do {
+    if (dev_alloc((void **)&Rslot, sizeof(double) * G * dd, st) != cudaSuccess ||
+        dev_alloc((void **)&Xslot, sizeof(double) * G * dd, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "tsqr_combine_r workspace");
+      break;
+    }
+    owned.insert(owned.end(), {(void *)Rslot, (void *)Xslot});
+    if (cudaMemcpyAsync(Rslot, Rin, sizeof(double) * G * dd, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      e = fail(CKINV_ECUDA, "tsqr_combine_r: copy of the R factors");
+      break;
+    }
+    std::vector<Stage<double>> sd(Hn);
+    for (int l = 0; l < Hn && !e.st; ++l) {
+      const Level &lv = levels[l];
+      const int P = (int)lv.top.size();
+      dim3 g((unsigned)std::min<int64_t>(ceil_div(2LL * d * d, 256), 256), P);
+      if ((e = alloc_stage<double>(sd[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
+      sd[l].stacked = true;
+      note_launch();
+      k_build_stack<double><<<g, 256, 0, st>>>(Rslot, sd[l].top, sd[l].bot, d, sd[l].M);
+      e = factor_stage<double>(ctx, sd[l], d, Rslot, st, true);
+    }
+    if (e.st) break;
+    note_launch();
+    k_finish_root<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 256), 256, 0, st>>>(Rslot, d, Rout,
+                                                                                                   Xslot);
+    double *Qs = nullptr, *Z1 = nullptr, *Z2 = nullptr;
+    const size_t qmax = std::max<size_t>(1, (size_t)G * 2 * dd);
+    if (dev_alloc((void **)&Qs, sizeof(double) * qmax, st) != cudaSuccess ||
+        dev_alloc((void **)&Z1, sizeof(double) * G * dd, st) != cudaSuccess ||
+        dev_alloc((void **)&Z2, sizeof(double) * G * dd, st) != cudaSuccess) {
+      e = fail(CKINV_ENOMEM, "tsqr_combine_r Q workspace");
+      break;
+    }
+    owned.insert(owned.end(), {(void *)Qs, (void *)Z1, (void *)Z2});
+    for (int l = Hn - 1; l >= 0 && !e.st; --l) {
+      const int P = (int)levels[l].top.size();
+      dim3 g((unsigned)std::min<int64_t>(ceil_div(2LL * d * d, 256), 256), P);
+      if ((e = apply_q<double>(ctx, sd[l], d, Xslot, Qs, Z1, Z2, st)).st) break;
+      note_launch();
+      k_scatter_x<double><<<g, 256, 0, st>>>(Qs, sd[l].top, sd[l].bot, d, Xslot);
+    }
+    if (e.st) break;
+    if (cudaMemcpyAsync(Xout, Xslot, sizeof(double) * G * dd, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      e = fail(CKINV_ECUDA, "tsqr_combine_r: copy of the Q blocks");
+    cudaError_t ce = cudaGetLastError();
+    if (e.st == CKINV_OK && ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
+  } while (0);
+  for (void *p : owned)
+    if (p) cudaFreeAsync(p, st);
+  return e;
+}
+
 }  // namespace ckinv

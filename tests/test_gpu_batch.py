@@ -175,3 +175,21 @@ def test_batched_problems_against_the_oracle(ctx):
         print("problem %d (n=%d d=%d): NLL err %.2e (bar %.2e), grad err %s (bar %s)" % (p, len(x), d, ev, tv, eg, tg))
         assert ev <= tv
         assert np.all(eg <= tg)
+
+
+def test_batched_graph_is_kept_and_relaunched(ctx):
+    """A second call with the same problems (descriptors and input pointers) relaunches the
+    kept graph: the same values, from the inputs' current contents."""
+    specs = synth.batch_specs(4, seed=5, n_lo=4096, n_hi=8192)
+    plans, kerns, pts, ys = _problems(specs)
+    v1, g1 = ck.nll_grad_batched(ctx, plans, kerns, pts, ys)
+    t0 = time.perf_counter()
+    v2, g2 = ck.nll_grad_batched(ctx, plans, kerns, pts, ys)
+    t_again = time.perf_counter() - t0
+    assert v1 == v2 and g1 == g2
+    ys[2].mul_(1.5)                                    # same pointer, new contents
+    v3, g3 = ck.nll_grad_batched(ctx, plans, kerns, pts, ys)
+    vs, gs = ck.nll_grad(ctx, plans[2], kerns[2], pts[2], ys[2])
+    _compare(v3[2], g3[2], vs, gs)
+    assert v3[0] == v1[0] and v3[2] != v1[2]
+    print("relaunch of the kept graph: %.1f ms" % (1e3 * t_again))
