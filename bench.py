@@ -372,6 +372,97 @@ def torch_from(a, dev):
     return torch.from_numpy(a).to(dev)
 
 
+def run_projection(ck, ctx, dev, n_new=4096):
+    """The paper's accuracy measure and prediction at the likelihood workload's size (n = 131072,
+    d = 384, SE l = 0.12): the second pass S = Q_hat^T K0 Q_hat with the column-space error
+    ||K0 - Q Q^T K0||_F / ||K0||_F (6 BF16 tensor-core products of the n x n x d contraction and
+    one FP32 pass over the n^2 kernel entries), the two-pass solve, and the predictive mean at
+    n_new new points (FP64 entries and sums).  Host wall clock around each call (the
+    column-space error is returned to the host); best of 3 after one untimed call."""
+    import torch
+    cfg = workload_config("c4_nll_n131072")
+    n, d, dim = cfg["n"], cfg["d"], cfg["dim"]
+    pts = torch_from(synth.points(n, dim, 0), dev)
+    y = torch_from(synth.gp_targets(synth.points(n, dim, 0), cfg["ell"], cfg["var"], cfg["tau"], seed=0), dev)
+    xnew = torch_from(synth.points(n_new, dim, 1), dev)
+    plan = ck.Plan(n=n, d=d, dim=dim, block_rows=cfg["block_rows"], prec=ck.BF16X3, seed=0, refine_steps=1)
+    kern = ck.Kernel(cfg["kind"], cfg["ell"], cfg["var"], cfg["tau"])
+    f = ck.tsqr(ctx, plan, kern, ck.sketch(ctx, plan, kern, pts))
+
+    def best(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return min(ts), r
+    t_proj, (_, err) = best(lambda: ck.project(ctx, f, plan, kern, pts))
+    alpha = ck.solve(ctx, f, y)
+    t_pred, _ = best(lambda: ck.predict_mean(ctx, plan, kern, pts, alpha, xnew))
+    ck.check(ctx)
+    flops = 6 * 2.0 * n * n * d
+    return {"workload": "c4_nll_n131072", "n": n, "d": d, "second_pass_ms": 1e3 * t_proj,
+            "second_pass_tflops": flops / t_proj / 1e12, "second_pass_flops": flops,
+            "colspace_rel_err": err, "predict_n_new": n_new, "predict_ms": 1e3 * t_pred,
+            "predict_fp64_kernel_evals_per_s": n * n_new / t_pred,
+            "timing": "host wall clock with a device synchronisation, best of 3 after one untimed call"}
+
+
+def run_blocking_simulation(ck, ctx, dev, sizes=(1000, 5000, 10000, 50000), d=512, m=16, tau=1e-3):
+    """The paper's blocking simulation (Sec. 5.1): K = E D E^T (E orthonormalised Gaussian,
+    eigenvalues exp(-0.01 i)) at n = 1000 .. 50000, solved through the materialised path with
+    each of the four Omega choices (Walsh-Hadamard, scaled Gaussian, Hartley, cosine), FP32
+    form.  K is built on the GPU from host-drawn factors (input generation, untimed; rank
+    min(n, 1024): the eigenvalues beyond are below exp(-10.24) = 3.6e-5 of the largest).
+    Per size and Omega: the solve (sketch, TSQR, core, refined solve of m right-hand sides)
+    timed with CUDA events (best of 2 after an untimed run) and the residual of its X against
+    that K on 48 sampled rows."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = {"d": d, "m": m, "nugget": tau, "rank": "min(n, 1024)",
+           "timing": "CUDA events, best of 2 after one untimed run"}
+    kinds = [("wht", ck.WHT), ("gaussian", ck.GAUSSIAN), ("hartley", ck.HARTLEY), ("cosine", ck.COSINE)]
+    for n in sizes:
+        E, D = synth.ede_factors(n, seed=0, rank=min(n, 1024))
+        Et = torch.from_numpy(E.astype(np.float32)).to(dev)
+        K = (Et * torch.from_numpy(D.astype(np.float32)).to(dev)[None, :]) @ Et.t()   # symmetric, n x n
+        del Et
+        A_np = synth.rhs(n, m, 0)
+        A = torch.from_numpy(np.ascontiguousarray(A_np.T)).to(dev).t()
+        rows = np.linspace(0, n - 1, 48).astype(np.int64)
+        Krows = K[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        rec = {}
+        for name, kind in kinds:
+            plan = ck.Plan(n=n, d=min(d, n // 2 // 16 * 16), block_rows=max(1024, 2 * d) if n >= 4 * d else 0,
+                           prec=ck.FP32, seed=0, refine_steps=1, omega_kind=kind)
+            dense = ck.Kernel(ck.DENSE, 0, 0, tau)
+            best, X = None, None
+            for r in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Y = ck.sketch(ctx, plan, dense, K=K.t())          # K is symmetric: its transpose view is column-major
+                f = ck.tsqr(ctx, plan, dense, Y)
+                X = ck.solve(ctx, f, A)
+                f.free()
+                e1.record(stream)
+                e1.synchronize()
+                if r:
+                    t = e0.elapsed_time(e1)
+                    best = t if best is None else min(best, t)
+            ck.check(ctx)
+            Xh = X.double().cpu().numpy()
+            res = Krows @ Xh + tau * Xh[rows] - A_np[rows]
+            rec[name] = {"ms_per_solve": best, "d": plan.d,
+                         "true_residual_sampled": float(np.linalg.norm(res) / np.linalg.norm(A_np[rows]))}
+        out["n%d" % n] = rec
+        del K
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(ck, ctx, dev):
     """The 64-problem batch: one ckinv_nll_grad_batched call (graph capture, instantiation,
     launch and read-back), timed by the host clock."""
@@ -413,6 +504,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg = workload_config(args.workload)
+    if args.block_rows:
+        cfg["block_rows"] = args.block_rows
     n, d, m, dim = cfg["n"], cfg["d"], cfg["m"], cfg["dim"]
     ctx = ck.Context(local_rank)
     prec = ck.PRECISIONS[args.prec]
@@ -550,6 +643,8 @@ def run_ours(args, rank, world, local_rank):
         extras["likelihood"] = run_likelihood(ck, ctx, dev)
         extras["materialised"] = run_materialised(ck, ctx, dev, stream, peaks)
         extras["batched"] = run_batched(ck, ctx, dev)
+        extras["projection"] = run_projection(ck, ctx, dev)
+        extras["blocking_simulation"] = run_blocking_simulation(ck, ctx, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -633,6 +728,7 @@ def main():
     ap.add_argument("--profile-kernel", default=None, choices=["sketch", "tsqr", "step"],
                     help="run only `steps` launches of one part of the step (for ncu captures): no JSON contract line")
     ap.add_argument("--n", type=int, default=None, help="override the workload's n (profiling a smaller case)")
+    ap.add_argument("--block-rows", type=int, default=None, help="override the workload's TSQR leaf height")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

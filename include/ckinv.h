@@ -85,7 +85,11 @@ typedef struct {
   int32_t tree_fp64_levels;/* top levels of the R tree combined in FP64; -1 = all.  Q_hat
                               is formed in the leaves' precision either way */
   int32_t leaf_fp64;       /* 1: per-block Householder (and so the whole tree) in FP64 */
-  int32_t reserved;        /* must be 0 */
+  int32_t omega_kind;      /* T of Omega = c R T P (Definition 1): 0 Walsh-Hadamard (the default,
+                              generated from bits on the fly); 1 the scaled Gaussian projection,
+                              2 discrete Hartley, 3 discrete cosine (Sec. 5.1's three choices;
+                              dense, materialised, for ckinv_sketch / ckinv_tsqr / ckinv_solve /
+                              ckinv_kinv_a only) */
 } ckinv_plan_desc;
 
 typedef struct ckinv_ctx ckinv_ctx;       /* workspaces, cached Omega, error string */
@@ -134,6 +138,17 @@ ckinv_status ckinv_set_wait_limit(ckinv_ctx *ctx, uint64_t nanoseconds);
  * 1 <= d <= min(N, 4096); P is drawn by a two-level radix select over the N keys. */
 ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed,
                          uint32_t *sign_bits, int32_t *cols, ckinv_stream stream);
+
+/* Omega as a dense n x d FP32 matrix (device, column-major, ldo >= n) of the given kind
+ * (0 Walsh-Hadamard, 1 scaled Gaussian, 2 discrete Hartley, 3 discrete cosine; see
+ * ckinv_plan_desc.omega_kind), each entry evaluated in FP64 and rounded once:
+ *   0: c r_k (-1)^popcount(k & p_j), c = N^-1/2, P over the N = 2^ceil(log2 n) columns;
+ *   1: z_kj / sqrt(n), z by Box-Muller from Philox words 0, 1 at (k d + j, stream 8);
+ *   2: n^-1/2 r_k cas(2 pi k p_j / n);   3: r_k s_p cos(pi (2k + 1) p_j / (2n)),
+ *      s_0 = n^-1/2, s_p = (2/n)^1/2; for 2 and 3 P is drawn over the n columns.
+ * Definition 1 (Sec. 3.2) and Sec. 5.1. */
+ckinv_status ckinv_omega_matrix(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, int32_t kind,
+                                float *Omega, int64_t ldo, ckinv_stream stream);
 
 /* The same draw as ckinv_omega for callers that cannot allocate device memory (for
  * example a program that reserves all device memory for its own pool up front, or code

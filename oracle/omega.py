@@ -70,3 +70,18 @@ def omega_rows(rows, n, d, seed, signs=None, cols=None):
 def omega_matrix(n, d, seed):
     """Omega = c R H_N P restricted to rows 0..n-1 (n x d, float64)."""
     return omega_rows(np.arange(n), n, d, seed)
+
+
+def gaussian_omega(n, d, seed):
+    """The scaled Gaussian projection the paper compares with (Sec. 2 and Sec. 5.1: "a matrix
+    with scaled iid standard Gaussian entries"): Omega[k, j] = z_kj / sqrt(n), z_kj standard
+    normal.  Reading (the paper fixes neither the generator nor the scale): z_kj by the
+    Box-Muller transform of the Philox4x32-10 words 0 and 1 at counter (k d + j, stream 8):
+    u = (w + 1/2) / 2^32, z = sqrt(-2 ln u_0) cos(2 pi u_1); the scale 1/sqrt(n) gives columns of
+    about unit norm (Omega's scale changes neither Q_hat nor K_N)."""
+    idx = np.arange(n * d, dtype=np.uint64)
+    w0, w1, _, _ = philox4x32_10(idx, 8, seed)
+    u0 = (w0.astype(np.float64) + 0.5) / 4294967296.0
+    u1 = (w1.astype(np.float64) + 0.5) / 4294967296.0
+    z = np.sqrt(-2.0 * np.log(u0)) * np.cos(2.0 * np.pi * u1)
+    return (z / np.sqrt(float(n))).reshape(n, d)

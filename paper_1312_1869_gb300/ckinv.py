@@ -22,6 +22,7 @@ STATUS_NAMES = ["CKINV_OK", "CKINV_EINVAL", "CKINV_ENOMEM", "CKINV_ECUDA", "CKIN
                 "CKINV_ETIMEOUT", "CKINV_EUNSUPPORTED"]
 SE, MATERN52, DENSE = 0, 1, 2
 FP32, BF16, BF16X2, BF16X3 = 0, 1, 2, 3
+WHT, GAUSSIAN, HARTLEY, COSINE = 0, 1, 2, 3       # Omega kinds
 PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x2": BF16X2, "bf16x3": BF16X3}
 
 
@@ -35,7 +36,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int32), ("d", ctypes.c_int32),
                 ("block_rows", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("refine_steps", ctypes.c_int32), ("tree_fp64_levels", ctypes.c_int32),
-                ("leaf_fp64", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("leaf_fp64", ctypes.c_int32), ("omega_kind", ctypes.c_int32)]
 
 
 class KernelDesc(ctypes.Structure):
@@ -53,6 +54,8 @@ _SIGS = {
     "ckinv_check": (ctypes.c_int, [_VP, _VP]),
     "ckinv_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "ckinv_omega": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
+    "ckinv_omega_matrix": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, _VP,
+                                          ctypes.c_int64, _VP]),
     "ckinv_omega_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, _VP, _VP, _VP]),
     "ckinv_sketch": (ctypes.c_int, [_VP, ctypes.POINTER(PlanDesc), ctypes.POINTER(KernelDesc), _VP, _VP,
                                     ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
@@ -152,10 +155,11 @@ class Plan:
     refine_steps: int = 1
     tree_fp64_levels: int = -1          # every level of the R tree combined in FP64
     leaf_fp64: int = 0
+    omega_kind: int = WHT
 
     def desc(self):
         return PlanDesc(self.n, self.dim, self.d, self.block_rows, self.prec, self.seed, self.refine_steps,
-                        self.tree_fp64_levels, self.leaf_fp64, 0)
+                        self.tree_fp64_levels, self.leaf_fp64, self.omega_kind)
 
 
 @dataclass
@@ -213,6 +217,13 @@ def omega(ctx, n, d, seed, stream=None):
     cols = torch.empty((d,), dtype=torch.int32, device="cuda")
     ctx._raise(load().ckinv_omega(ctx.handle, n, d, seed, _ptr(bits), _ptr(cols), _stream(stream)))
     return bits, cols
+
+
+def omega_matrix(ctx, n, d, seed, kind=WHT, stream=None):
+    """Omega as a dense column-major n x d float32 tensor."""
+    Om = colmajor(n, d)
+    ctx._raise(load().ckinv_omega_matrix(ctx.handle, n, d, seed, kind, _ptr(Om), n, _stream(stream)))
+    return Om
 
 
 def omega_noalloc(n, d, seed, sign_bits=None, cols=None, stream=None):

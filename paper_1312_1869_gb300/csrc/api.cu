@@ -139,6 +139,7 @@ Error check_plan(const ckinv_plan_desc *plan, const ckinv_kernel *kern, bool nee
   if (plan->refine_steps < 0 || plan->refine_steps > 4) return fail(CKINV_EINVAL, "refine_steps must be 0..4");
   if (plan->tree_fp64_levels < -1) return fail(CKINV_EINVAL, "tree_fp64_levels must be >= -1");
   if (plan->leaf_fp64 != 0 && plan->leaf_fp64 != 1) return fail(CKINV_EINVAL, "leaf_fp64 must be 0 or 1");
+  if (plan->omega_kind < 0 || plan->omega_kind > 3) return fail(CKINV_EINVAL, "omega_kind must be 0..3");
   return ok();
 }
 
@@ -225,8 +226,26 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
     return fail(CKINV_EINVAL, "points must be non-null");
   }
   if (kern->kind != CKINV_DENSE) CK_TRY(check_finite(ctx, points, plan->dim, plan->n, plan->dim, st));
-  CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   KernelParams kp = make_params(plan, kern);
+  if (plan->omega_kind != 0) {
+    // a dense Omega (Gaussian, Hartley or cosine): materialised, then contracted
+    if (deriv) return fail(CKINV_EINVAL, "the derivative sketch takes the Walsh-Hadamard Omega only");
+    if (kern->kind != CKINV_DENSE && (row0 != 0 || m != plan->n))
+      return fail(CKINV_EINVAL, "a row range of a matrix-free sketch takes the Walsh-Hadamard Omega only");
+    float *Om = nullptr;
+    CK_CUDA(dev_alloc(&Om, sizeof(float) * (size_t)plan->n * plan->d, st));
+    Error e = omega_dense(ctx, plan->n, plan->d, plan->seed, plan->omega_kind, Om, st);
+    if (e.st == CKINV_OK) {
+      if (kern->kind == CKINV_DENSE)
+        e = gemm_batched<float>(ctx, false, (int)m, plan->d, (int)plan->n, 1.0f, K + row0, ldk, 0, Om, plan->n, 0, 0.0f,
+                                Y, ldy, 0, 1, st);
+      else
+        e = sketch_dense_omega(ctx, plan->n, plan->dim, plan->d, kp, points, Om, Y, ldy, st);
+    }
+    cudaFreeAsync(Om, st);
+    return e;
+  }
+  CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   if (kern->kind == CKINV_DENSE) {
     // K is symmetric: its column i is read as row i (16-byte rows for the tensor-core path)
     if (plan->prec != CKINV_FP32 && ldk % 4 == 0 && (reinterpret_cast<uintptr_t>(K) & 15) == 0)
@@ -242,7 +261,7 @@ void factor_release(ckinv_factor *f) {
   if (!f) return;
   for (void *p : {(void *)f->Q, (void *)f->R, (void *)f->B, (void *)f->Cp, (void *)f->luB, (void *)f->pivB,
                   (void *)f->logdet_parts, (void *)f->bits, (void *)f->cols, (void *)f->S2, (void *)f->pivS,
-                  (void *)f->logdet2})
+                  (void *)f->logdet2, (void *)f->omega_dense})
     if (p) cudaFreeAsync(p, f->stream);
   delete f;
 }
@@ -292,6 +311,10 @@ Error autotune_leaf_rows(ckinv_ctx *ctx, const ckinv_plan_desc *plan, cudaStream
   std::vector<int> cand;
   for (int b : {256, 512, 1024, 2048, 4096})
     if (b >= d && (int64_t)b * 2 <= n) cand.push_back(b);
+  // the tallest leaf whose panels fit in shared memory (fewer leaves, fewer FP64 combines)
+  const int bmax = max_leaf_rows(d, plan->leaf_fp64 != 0);
+  if (bmax >= d && (int64_t)bmax * 2 <= n && std::find(cand.begin(), cand.end(), bmax) == cand.end())
+    cand.push_back(bmax);
   if (cand.empty()) cand.push_back(auto_block_rows(n, d, ctx->sm_count));
   float *Y = nullptr, *Q = nullptr;
   double *R = nullptr;
@@ -389,6 +412,11 @@ Error do_tsqr(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *k
     cudaError_t c2 = cudaMemcpyAsync(f->cols, ctx->om.cols, sizeof(int32_t) * d, cudaMemcpyDeviceToDevice, st);
     if (c1 != cudaSuccess || c2 != cudaSuccess) e = fail(CKINV_ECUDA, "copy of Omega into the factor failed");
   }
+  if (e.st == CKINV_OK && plan->omega_kind != 0) {
+    f->omega_kind = plan->omega_kind;
+    alloc((void **)&f->omega_dense, sizeof(float) * (size_t)n * d);
+    if (e.st == CKINV_OK) e = omega_dense(ctx, n, d, plan->seed, plan->omega_kind, f->omega_dense, st);
+  }
   if (e.st == CKINV_OK) {
     e = tsqr_factor(ctx, n, d, b, plan->tree_fp64_levels, plan->leaf_fp64 != 0, tsqr_on_tensor_cores(plan), Y, ldy, f->Q,
                     f->R, st);
@@ -483,6 +511,7 @@ Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_
   CK_TRY(check_plan(plan, kern, true));
   if (kern->kind == CKINV_DENSE) return fail(CKINV_EINVAL, "nll_grad needs a kernel function, not a matrix");
   if (!points || !y || !out_dev) return fail(CKINV_EINVAL, "null argument");
+  if (plan->omega_kind != 0) return fail(CKINV_EINVAL, "the likelihood takes the Walsh-Hadamard Omega only");
   const int64_t n = plan->n;
   const int d = plan->d;
   const size_t dd = (size_t)d * d;
@@ -888,6 +917,26 @@ ckinv_status ckinv_omega(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, ui
   return finish(ctx, e);
 }
 
+ckinv_status ckinv_omega_matrix(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, int32_t kind, float *Omega,
+                                int64_t ldo, ckinv_stream stream) {
+  if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
+  if (!Omega || n < 1 || d < 1 || ldo < n || kind < 0 || kind > 3 || d > 4096 ||
+      (int64_t)d > (kind == 0 ? padded_order(n) : n))
+    return finish(ctx, fail(CKINV_EINVAL, "need Omega, ldo >= n, 0 <= kind <= 3, 1 <= d <= min(4096, N or n)"));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ldo == n) return finish(ctx, omega_dense(ctx, n, d, seed, kind, Omega, st));
+  float *tmp = nullptr;
+  if (dev_alloc(&tmp, sizeof(float) * (size_t)n * d, st) != cudaSuccess)
+    return finish(ctx, fail(CKINV_ENOMEM, "Omega workspace"));
+  Error e = omega_dense(ctx, n, d, seed, kind, tmp, st);
+  if (e.st == CKINV_OK && cudaMemcpy2DAsync(Omega, sizeof(float) * ldo, tmp, sizeof(float) * n, sizeof(float) * n, d,
+                                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    e = fail(CKINV_ECUDA, "copy of Omega failed");
+  cudaFreeAsync(tmp, st);
+  return finish(ctx, e);
+}
+
 ckinv_status ckinv_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel *kern, const float *points,
                           const float *K, int64_t ldk, float *Y, int64_t ldy, ckinv_stream stream) {
   if (!ctx) return finish(nullptr, fail(CKINV_EINVAL, "null context"));
@@ -981,6 +1030,7 @@ ckinv_status ckinv_tsqr_shard(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const
   Error e = check_plan(plan, kern, false);
   if (e.st == CKINV_OK && (!Y || !out || !R_local || row0 < 0 || m < plan->d || row0 + m > plan->n || ldy < m))
     e = fail(CKINV_EINVAL, "need Y, out, R_local, 0 <= row0, d <= m, row0 + m <= n, ldy >= m");
+  if (e.st == CKINV_OK && plan->omega_kind != 0) e = fail(CKINV_EINVAL, "row shards take the Walsh-Hadamard Omega only");
   if (e.st) return finish(ctx, e);
   *out = nullptr;
   const int d = plan->d;
@@ -1116,6 +1166,7 @@ ckinv_status ckinv_factor_project(ckinv_ctx *ctx, ckinv_factor *f, const ckinv_p
   if (e.st == CKINV_OK && (kern->kind == CKINV_DENSE || !points))
     e = fail(CKINV_EINVAL, "the second pass needs points and a kernel function");
   if (e.st == CKINV_OK && (plan->n != f->n || plan->d != f->d)) e = fail(CKINV_EINVAL, "plan does not match the factor");
+  if (e.st == CKINV_OK && f->n_total != 0) e = fail(CKINV_EINVAL, "a shard factor has no second pass");
   cudaStream_t st = (cudaStream_t)stream;
   if (e.st == CKINV_OK) e = check_finite(ctx, points, plan->dim, plan->n, plan->dim, st);
   if (e.st == CKINV_OK) e = two_pass_core(ctx, f, plan->dim, make_params(plan, kern), points, colspace_err, st);

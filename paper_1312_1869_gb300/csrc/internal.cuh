@@ -153,6 +153,9 @@ struct ckinv_factor {
   // n_total points; Omega's signs and columns are those of the whole problem
   int64_t row0 = 0;
   int64_t n_total = 0;
+  // Omega of a kind other than the bit-generated Walsh-Hadamard one: dense n x d FP32 copy
+  int omega_kind = 0;
+  float *omega_dense = nullptr;
 };
 
 namespace ckinv {
@@ -183,6 +186,14 @@ Error stage_upload(ckinv_ctx *ctx, const void *src, size_t bytes, void *dst, cud
 // ----------------------------------------------------------------------------- Omega
 Error omega_draw(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, cudaStream_t st);
 Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st);   // ctx->om.omegaT
+// Omega as a dense n x d FP32 matrix (ld n) of kind 0 Walsh-Hadamard, 1 scaled Gaussian,
+// 2 discrete Hartley, 3 discrete cosine (T of Definition 1, or Sec. 5.1's Gaussian projection).
+Error omega_dense(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, int kind, float *Om, cudaStream_t st);
+// Y = var * K0 Omega for a dense Omega (n x d FP32): the fused tensor-core sketch with Omega in
+// three BF16 terms and kernel entries in three, eight of the nine term products, partial sums
+// over 4096-point ranges folded in FP64.
+Error sketch_dense_omega(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points,
+                         const float *Om, float *Y, int64_t ldy, cudaStream_t st);
 // Grows the context's Omega buffers and draw scratch to hold an (n, d) draw (no draw).
 Error omega_reserve(ckinv_ctx *ctx, int64_t n, int32_t d, cudaStream_t st);
 
@@ -214,6 +225,8 @@ struct TsqrOut {
 Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
                   const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
 int auto_block_rows(int64_t n, int d, int sm_count);
+// Tallest TSQR leaf (a multiple of 16) whose panels fit in shared memory at this d.
+int max_leaf_rows(int d, bool leaf_fp64);
 // Tree combine of G given R factors (FP64, strided d x d): root R (diag >= 0) and each leaf's
 // d x d block of the combined Q factor.
 Error tsqr_combine_r(ckinv_ctx *ctx, int G, int d, const double *Rin, double *Rout, double *Xout, cudaStream_t st);

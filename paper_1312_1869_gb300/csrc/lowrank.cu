@@ -794,7 +794,9 @@ Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
   // B = Omega^T Q_hat  (B^T = Q_hat^T Omega: rows of A are the columns of Q_hat).  The BF16
   // form uses the tensor cores with Q_hat split into three BF16 terms (~1e-5 relative); the
   // other forms keep the FP32-accurate contraction (FP64 across 256-row chunks)
-  if (f->n % 4 == 0 && f->prec == CKINV_BF16)
+  if (f->omega_dense)        // a dense Omega (Gaussian, Hartley, cosine): B = Omega^T Q_hat in FP32
+    CK_TRY(tsprod(ctx, f->n, d, d, f->omega_dense, f->n, nullptr, nullptr, 0.0, f->Q, f->n, f->B, st));
+  else if (f->n % 4 == 0 && f->prec == CKINV_BF16)
     CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
   else
     CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));

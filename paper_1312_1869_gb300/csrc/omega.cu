@@ -204,7 +204,82 @@ Error select_columns(int64_t N, int d, uint32_t k0, uint32_t k1, int grid, uint3
   return ok();
 }
 
+// Dense Omega (n x d FP32, column-major, ld n) of a given kind (Definition 1's c R T P with T
+// the Walsh-Hadamard, discrete Hartley or cosine matrix, or the scaled Gaussian projection
+// of Sec. 5.1), each entry evaluated in FP64 and rounded once.  Readings:
+//   Walsh-Hadamard  c r_k (-1)^popcount(k & p_j),  c = N^-1/2
+//   Hartley         n^-1/2 r_k cas(2 pi (k p_j mod n) / n),  cas = cos + sin
+//   cosine          r_k s_p cos(pi ((2k + 1) p_j mod 4n) / (2n)),  s_0 = n^-1/2, s_p = (2/n)^1/2
+//   Gaussian        z_kj / sqrt(n), z by Box-Muller from Philox words 0, 1 at (k d + j, stream 8)
+__global__ void k_omega_dense(int64_t n, int d, int kind, double c, uint32_t k0, uint32_t k1,
+                              const uint32_t *__restrict__ bits, const int32_t *__restrict__ cols,
+                              float *__restrict__ Om) {
+  const int j = blockIdx.y;
+  const int64_t p = kind == 1 ? 0 : (int64_t)cols[j];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (kind == 1) {
+      const uint64_t idx = (uint64_t)k * (uint64_t)d + (uint64_t)j;
+      const uint4 w = dev::philox4x32_10((uint32_t)idx, (uint32_t)(idx >> 32), 8u, 0u, k0, k1);
+      const double u0 = ((double)w.x + 0.5) * (1.0 / 4294967296.0);
+      const double u1 = ((double)w.y + 0.5) * (1.0 / 4294967296.0);
+      v = sqrt(-2.0 * log(u0)) * cospi(2.0 * u1) * c;
+    } else {
+      const double r = ((bits[k >> 5] >> (k & 31)) & 1u) ? -1.0 : 1.0;
+      if (kind == 0) {
+        v = (__popcll((unsigned long long)(k & p)) & 1) ? -c * r : c * r;
+      } else if (kind == 2) {
+        const double a = (double)(((k % n) * (p % n)) % n) / (double)n;   // angle / (2 pi)
+        v = c * r * (cospi(2.0 * a) + sinpi(2.0 * a));
+      } else {
+        const int64_t m = ((2 * k + 1) * p) % (4 * n);
+        const double s = (p == 0) ? sqrt(1.0 / (double)n) : sqrt(2.0 / (double)n);
+        v = r * s * cospi((double)m / (2.0 * (double)n));
+      }
+    }
+    Om[k + (int64_t)j * n] = (float)v;
+  }
+}
+
 }  // namespace
+
+Error omega_dense(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, int kind, float *Om, cudaStream_t st) {
+  if (kind < 0 || kind > 3) return fail(CKINV_EINVAL, "unknown Omega kind");
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  // the signs of R and the column subsample: over N = 2^ceil(log2 n) candidates for the
+  // Walsh-Hadamard matrix, over the n columns of the Hartley and cosine matrices
+  const uint32_t *bits = nullptr;
+  const int32_t *cols = nullptr;
+  if (kind == 0) {
+    CK_TRY(omega_draw(ctx, n, d, seed, st));
+    bits = ctx->om.bits;
+    cols = ctx->om.cols;
+  } else if (kind >= 2) {
+    if (d > n) return fail(CKINV_EINVAL, "d above n for a Hartley or cosine Omega");
+    CK_TRY(omega_draw(ctx, n, d, seed, st));          // signs (and scratch) for this n
+    bits = ctx->om.bits;
+    int32_t *c2 = nullptr;
+    CK_CUDA(dev_alloc(&c2, sizeof(int32_t) * d, st));
+    const int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->sm_count * 8);
+    Error e = select_columns(n, d, k0, k1, grid, ctx->hist, ctx->small, ctx->cand, ctx->cand_idx,
+                             (uint32_t)ctx->cand_cap, c2, ctx->d_err, st);
+    if (e.st) {
+      cudaFreeAsync(c2, st);
+      return e;
+    }
+    cols = c2;
+  }
+  double c = 1.0;
+  if (kind == 0) c = 1.0 / std::sqrt((double)padded_order(n));
+  else if (kind == 1 || kind == 2) c = 1.0 / std::sqrt((double)n);
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 256), (unsigned)d);
+  note_launch();
+  k_omega_dense<<<grid, 256, 0, st>>>(n, d, kind, c, k0, k1, bits, cols, Om);
+  cudaError_t ce = cudaGetLastError();
+  if (kind >= 2) cudaFreeAsync(const_cast<int32_t *>(cols), st);
+  if (ce != cudaSuccess) return fail(CKINV_ECUDA, cudaGetErrorString(ce));
+  return ok();
+}
 
 namespace {
 template <typename T>

@@ -241,6 +241,53 @@ Error two_pass_core(ckinv_ctx *ctx, ckinv_factor *f, int dim, const KernelParams
   return ok();
 }
 
+// W (n x d) = var * K0 M for a dense right factor M (n x d FP32, ld ldm), FP32-accurate up to the
+// tensor cores' accumulation over 4096-point ranges: M and the kernel entries in three BF16
+// terms each.
+static Error kernel_times_dense(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp,
+                                const float *points, const float *M, int64_t ldm, float *W, int64_t ldw,
+                                cudaStream_t st) {
+  const int64_t kpad = ceil_div(n, 64) * 64;
+  const int num_kb = (int)(kpad / 64);
+  const int splits = (int)ceil_div(num_kb, kMaxBlocksPerSplit);
+  const int64_t ldp = ceil_div(n, 128) * 128;
+  __nv_bfloat16 *Bt = nullptr;
+  float *part = nullptr;
+  CK_CUDA(dev_alloc(&Bt, sizeof(__nv_bfloat16) * 3 * d * kpad, st));
+  if (dev_alloc(&part, sizeof(float) * (size_t)splits * ldp * d, st) != cudaSuccess) {
+    cudaFreeAsync(Bt, st);
+    return fail(CKINV_ENOMEM, "dense-Omega sketch workspace");
+  }
+  Error e = ok();
+  note_launch();
+  k_split_terms<<<dim3((unsigned)std::min<int64_t>(ceil_div(kpad, 256), 1024), d), 256, 0, st>>>(n, d, M, ldm, kpad,
+                                                                                                 Bt);
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
+  // eight of the nine term products: all but (third term of the entry) x (third term of
+  // Omega).  With a dense Omega of random signs Y's entries cancel (|Y| well below the sum of
+  // its terms' magnitudes), so the order-three products (2^-24 relative each) are kept.
+  const int terms_of_entry[3] = {3, 3, 2};
+  for (int t = 0; t < 3 && !e.st; ++t)
+    e = sketch_tc_rhs(ctx, n, dim, d, terms_of_entry[t], kp, points, Bt + (size_t)t * d * kpad, kpad, splits, part, ldp,
+                      t > 0, st);
+  if (!e.st) {
+    note_launch();
+    k_fold_parts_f32<<<(unsigned)std::min<int64_t>(ceil_div(n * d, 256), 4096), 256, 0, st>>>(n, d, splits, part, ldp,
+                                                                                              kp.var, W, ldw);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
+  }
+  cudaFreeAsync(Bt, st);
+  cudaFreeAsync(part, st);
+  return e;
+}
+
+Error sketch_dense_omega(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points,
+                         const float *Om, float *Y, int64_t ldy, cudaStream_t st) {
+  return kernel_times_dense(ctx, n, dim, d, kp, points, Om, n, Y, ldy, st);
+}
+
 Error predict_mean(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, const float *alpha,
                    const float *xnew, int64_t n_new, double *mean, cudaStream_t st) {
   note_launch();

@@ -1084,6 +1084,8 @@ int max_block_rows(int d, bool leaf_fp64) {
 
 }  // namespace
 
+int max_leaf_rows(int d, bool leaf_fp64) { return max_block_rows(d, leaf_fp64); }
+
 int auto_block_rows(int64_t n, int d, int sm_count) {
   (void)sm_count;
   int64_t b = 2048;

@@ -184,3 +184,19 @@ def test_two_pass_with_transposed_product_is_caught():
     bad = (A - Q @ V) / tau
     good = pr.two_pass_solve(Q, S, tau, A)
     assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
+
+
+def test_gaussian_omega_is_standard_normal_and_scaled():
+    """The Gaussian projection's entries pass a Kolmogorov-Smirnov test against the standard
+    normal (after the 1/sqrt(n) scale is undone), are independent across entries (lag-1
+    correlation), and its columns are nearly orthonormal for large n."""
+    from scipy import stats
+    from oracle import omega as om
+    n, d = 4000, 64
+    O = om.gaussian_omega(n, d, 5)
+    z = (O * np.sqrt(n)).ravel()
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) < 0.02
+    G = O.T @ O
+    assert np.abs(np.diag(G) - 1.0).max() < 0.1 and np.abs(G - np.diag(np.diag(G))).max() < 0.1
+    assert not np.array_equal(O, om.gaussian_omega(n, d, 6))
