@@ -274,7 +274,8 @@ def run_likelihood(ck, ctx, dev, reps=3):
     gold = golden_likelihood()
     out = {"workload": "c4_nll_n131072", "n": n, "d": d,
            "timing": "host wall clock around the call (it returns host scalars), median of %d" % reps}
-    for name, prec, leaf64 in [("bf16x3", ck.BF16X3, 0), ("bf16x3_fp64_leaves", ck.BF16X3, 1), ("bf16", ck.BF16, 0)]:
+    for name, prec, leaf64 in [("bf16x3", ck.BF16X3, 0), ("bf16x3_fp64_leaves", ck.BF16X3, 1), ("bf16", ck.BF16, 0),
+                               ("fp32_wht", ck.FP32_WHT, 0), ("fp32_wht_fp64_leaves", ck.FP32_WHT, 1)]:
         plan = ck.Plan(n=n, d=d, dim=dim, block_rows=cfg["block_rows"], prec=prec, seed=cfg["seed"], refine_steps=1,
                        tree_fp64_levels=-1, leaf_fp64=leaf64)
         ck.nll_grad(ctx, plan, kern, pts, y)
@@ -614,7 +615,7 @@ def run_ours(args, rank, world, local_rank):
         forms = {}
         for name, prec, lv in [("bf16", args.prec, args.fp64_levels), ("bf16x2", "bf16x2", args.fp64_levels),
                                ("bf16x3", "bf16x3", args.fp64_levels), ("fp32", "fp32", args.fp64_levels),
-                               ("bf16_fp32_tree", args.prec, 0)]:
+                               ("fp32_wht", "fp32_wht", args.fp64_levels), ("bf16_fp32_tree", args.prec, 0)]:
             plan2 = ck.Plan(n=n, d=d, dim=dim, block_rows=cfg["block_rows"], prec=ck.PRECISIONS[prec], seed=5,
                             refine_steps=args.refine, tree_fp64_levels=lv)
             best = None
@@ -696,7 +697,10 @@ def run_profile(args):
     Y = ck.colmajor(n, d)
     X = ck.colmajor(n, m)
     ck.sketch(ctx, plan, kern, pts, Y=Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            e0.record()
         if args.profile_kernel in ("sketch", "step"):
             ck.sketch(ctx, plan, kern, pts, Y=Y)
         if args.profile_kernel in ("tsqr", "step"):
@@ -704,10 +708,12 @@ def run_profile(args):
             if args.profile_kernel == "step":
                 ck.solve(ctx, f, A, X)
             f.free()
+    e1.record()
     torch.cuda.synchronize()
     ck.check(ctx)
     print(json.dumps({"profile": args.profile_kernel, "n": n, "d": d, "prec": args.prec,
-                      "launches": args.warmup + args.steps}), flush=True)
+                      "launches": args.warmup + args.steps,
+                      "ms_per_iteration": e0.elapsed_time(e1) / args.steps if args.steps else None}), flush=True)
     ctx.close()
 
 
@@ -718,7 +724,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3_bf16_n262144")
-    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x2", "bf16x3"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x2", "bf16x3", "fp32_wht"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--fp64-levels", type=int, default=-1, help="tree levels combined in FP64 (-1: all)")
     ap.add_argument("--ref-rows", type=int, default=2048, help="sketch rows in the oracle's timed sample")

@@ -63,7 +63,11 @@ typedef enum {
   CKINV_FP32 = 0,          /* kernel tile x Omega in FP32 FMA (SIMT) */
   CKINV_BF16 = 1,          /* one BF16 tensor-core product, FP32 accumulation */
   CKINV_BF16X2 = 2,        /* kernel tile split in two BF16 terms (two products) */
-  CKINV_BF16X3 = 3         /* three BF16 terms: FP32-accurate on tensor cores */
+  CKINV_BF16X3 = 3,        /* three BF16 terms: FP32-accurate on tensor cores */
+  CKINV_FP32_WHT = 4       /* FP32 on the CUDA cores through the fast Walsh-Hadamard transform
+                              (Sec. 3.2's structured Omega applied as a transform: per kernel
+                              entry log2(1024) additions instead of 2d multiply-adds); needs
+                              omega_kind 0 and N >= 1024, else the same as CKINV_FP32 */
 } ckinv_precision;
 
 typedef struct {

@@ -21,9 +21,9 @@ OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT, EUNSUPPORTED = range(7)
 STATUS_NAMES = ["CKINV_OK", "CKINV_EINVAL", "CKINV_ENOMEM", "CKINV_ECUDA", "CKINV_ESINGULAR",
                 "CKINV_ETIMEOUT", "CKINV_EUNSUPPORTED"]
 SE, MATERN52, DENSE = 0, 1, 2
-FP32, BF16, BF16X2, BF16X3 = 0, 1, 2, 3
+FP32, BF16, BF16X2, BF16X3, FP32_WHT = 0, 1, 2, 3, 4
 WHT, GAUSSIAN, HARTLEY, COSINE = 0, 1, 2, 3       # Omega kinds
-PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x2": BF16X2, "bf16x3": BF16X3}
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "bf16x2": BF16X2, "bf16x3": BF16X3, "fp32_wht": FP32_WHT}
 
 
 class CKInvError(RuntimeError):

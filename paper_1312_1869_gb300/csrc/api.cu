@@ -134,7 +134,7 @@ Error check_plan(const ckinv_plan_desc *plan, const ckinv_kernel *kern, bool nee
       return fail(CKINV_EINVAL, "lengthscale and variance must be > 0");
   }
   if (!(kern->nugget > 0)) return fail(CKINV_EINVAL, "nugget must be > 0");
-  if (plan->prec < CKINV_FP32 || plan->prec > CKINV_BF16X3) return fail(CKINV_EINVAL, "unknown precision");
+  if (plan->prec < CKINV_FP32 || plan->prec > CKINV_FP32_WHT) return fail(CKINV_EINVAL, "unknown precision");
   if (plan->block_rows != 0 && plan->block_rows < plan->d) return fail(CKINV_EINVAL, "block_rows must be >= d");
   if (plan->refine_steps < 0 || plan->refine_steps > 4) return fail(CKINV_EINVAL, "refine_steps must be 0..4");
   if (plan->tree_fp64_levels < -1) return fail(CKINV_EINVAL, "tree_fp64_levels must be >= -1");
@@ -248,11 +248,14 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
   CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   if (kern->kind == CKINV_DENSE) {
     // K is symmetric: its column i is read as row i (16-byte rows for the tensor-core path)
-    if (plan->prec != CKINV_FP32 && ldk % 4 == 0 && (reinterpret_cast<uintptr_t>(K) & 15) == 0)
+    if (plan->prec != CKINV_FP32 && plan->prec != CKINV_FP32_WHT && ldk % 4 == 0 &&
+        (reinterpret_cast<uintptr_t>(K) & 15) == 0)
       return dense_tc(ctx, m, plan->n, plan->d, plan->prec, K + row0 * ldk, ldk, kp.scale, Y, ldy, nullptr, 0, 0, st);
     return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, nullptr, K, ldk, false, Y, ldy, st, row0, m);
   }
-  if (plan->prec == CKINV_FP32)
+  if (plan->prec == CKINV_FP32_WHT && sketch_wht_supported(plan->n, plan->d))
+    return sketch_wht(ctx, plan->n, plan->dim, plan->d, kp, points, deriv, Y, ldy, st, row0, m);
+  if (plan->prec == CKINV_FP32 || plan->prec == CKINV_FP32_WHT)
     return sketch_simt(ctx, plan->n, plan->dim, plan->d, kp, points, nullptr, 0, deriv, Y, ldy, st, row0, m);
   return sketch_tc(ctx, plan->n, plan->dim, plan->d, plan->prec, kp, points, deriv, Y, ldy, st, row0, m);
 }

@@ -190,8 +190,8 @@ Error omega_materialise_bf16(ckinv_ctx *ctx, cudaStream_t st);   // ctx->om.omeg
 // 2 discrete Hartley, 3 discrete cosine (T of Definition 1, or Sec. 5.1's Gaussian projection).
 Error omega_dense(ckinv_ctx *ctx, int64_t n, int32_t d, uint64_t seed, int kind, float *Om, cudaStream_t st);
 // Y = var * K0 Omega for a dense Omega (n x d FP32): the fused tensor-core sketch with Omega in
-// three BF16 terms and kernel entries in three, eight of the nine term products, partial sums
-// over 4096-point ranges folded in FP64.
+// three BF16 terms and kernel entries in three, the six term products of order <= 2, partial
+// sums over 4096-point ranges folded in FP64.
 Error sketch_dense_omega(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points,
                          const float *Om, float *Y, int64_t ldy, cudaStream_t st);
 // Grows the context's Omega buffers and draw scratch to hold an (n, d) draw (no draw).
@@ -207,6 +207,11 @@ Error sketch_simt(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams 
 // from the FP32 points and rounded once.
 Error kernel_matrix(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, const float *points, float *K,
                     int64_t ldk, cudaStream_t st);
+// Rows row0 .. row0 + m - 1 of Y = K0 Omega through the fast Walsh-Hadamard transform, FP32 on
+// the CUDA cores (needs N = 2^ceil(log2 n) >= 1024 and d <= 512).
+bool sketch_wht_supported(int64_t n, int d);
+Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points, bool deriv,
+                 float *Y, int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
                 int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);

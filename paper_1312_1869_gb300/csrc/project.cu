@@ -264,10 +264,9 @@ static Error kernel_times_dense(ckinv_ctx *ctx, int64_t n, int dim, int d, const
                                                                                                  Bt);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
-  // eight of the nine term products: all but (third term of the entry) x (third term of
-  // Omega).  With a dense Omega of random signs Y's entries cancel (|Y| well below the sum of
-  // its terms' magnitudes), so the order-three products (2^-24 relative each) are kept.
-  const int terms_of_entry[3] = {3, 3, 2};
+  // the six term products of order at most two (keeping the two of order three changed the
+  // measured error by nothing: the tensor cores' accumulation sets it)
+  const int terms_of_entry[3] = {3, 2, 1};
   for (int t = 0; t < 3 && !e.st; ++t)
     e = sketch_tc_rhs(ctx, n, dim, d, terms_of_entry[t], kp, points, Bt + (size_t)t * d * kpad, kpad, splits, part, ldp,
                       t > 0, st);

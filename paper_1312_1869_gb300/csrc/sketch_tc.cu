@@ -468,6 +468,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = (uint32_t)(g * 32 * kRowsPerLane + lane) * kRowBytes;
     bool good = true;
     // one block: wait for its points and for the stage, fill the stage's A tiles
+    // dense mode: the 32 entries of this lane's row for block kb, into nxt (zero past n)
+    float nxt[kRowsPerLane][CH * 8];
+    auto load_dense = [&](int kb) {
+      const int64_t kbase = (int64_t)(kb_begin + kb) * BK + h * KH;
+#pragma unroll
+      for (int r = 0; r < kRowsPerLane; ++r) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const int64_t k0 = kbase + c * 8;
+          if (rok[r] && k0 + 8 <= a.n) {
+            const float4 lo = *reinterpret_cast<const float4 *>(arow[r] + k0);
+            const float4 hi = *reinterpret_cast<const float4 *>(arow[r] + k0 + 4);
+            nxt[r][c * 8 + 0] = lo.x; nxt[r][c * 8 + 1] = lo.y; nxt[r][c * 8 + 2] = lo.z; nxt[r][c * 8 + 3] = lo.w;
+            nxt[r][c * 8 + 4] = hi.x; nxt[r][c * 8 + 5] = hi.y; nxt[r][c * 8 + 6] = hi.z; nxt[r][c * 8 + 7] = hi.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) nxt[r][c * 8 + u] = (rok[r] && k0 + u < a.n) ? arow[r][k0 + u] : 0.0f;
+          }
+        }
+      }
+    };
+    if (MODE == 1 && nkb > 0) load_dense(0);
     auto produce = [&](int kb) -> bool {
       int s = kb % S;
       uint32_t ph = (uint32_t)(kb / S) & 1u;
@@ -513,22 +535,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
+        // dense mode: this block's rows of A were loaded while the previous block was stored;
+        // the next block's loads go out now and land during this block's stores and waits
 #pragma unroll
-        for (int r = 0; r < kRowsPerLane; ++r) {
+        for (int r = 0; r < kRowsPerLane; ++r)
 #pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int64_t k0 = kbase + c * 8;
-            if (rok[r] && k0 + 8 <= a.n) {
-              float4 lo = *reinterpret_cast<const float4 *>(arow[r] + k0);
-              float4 hi = *reinterpret_cast<const float4 *>(arow[r] + k0 + 4);
-              kv[r][c * 8 + 0] = lo.x; kv[r][c * 8 + 1] = lo.y; kv[r][c * 8 + 2] = lo.z; kv[r][c * 8 + 3] = lo.w;
-              kv[r][c * 8 + 4] = hi.x; kv[r][c * 8 + 5] = hi.y; kv[r][c * 8 + 6] = hi.z; kv[r][c * 8 + 7] = hi.w;
-            } else {
-#pragma unroll
-              for (int u = 0; u < 8; ++u) kv[r][c * 8 + u] = (rok[r] && k0 + u < a.n) ? arow[r][k0 + u] : 0.0f;
-            }
-          }
-        }
+          for (int u = 0; u < CH * 8; ++u) kv[r][u] = nxt[r][u];
+        if (kb + 1 < nkb) load_dense(kb + 1);
       }
       // Phase 2: split into BF16 terms and store each 16-byte chunk at its swizzled place.
       uint8_t *stage_base = tiles + (size_t)s * stage_bytes;

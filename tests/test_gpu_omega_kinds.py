@@ -5,7 +5,9 @@ the blocking simulation's covariance K = E D E^T (Sec. 5.1) through the material
 Bars: Omega entrywise to FP32 rounding (each entry is evaluated in FP64 and rounded once on
 the GPU: |diff| <= 2^-24 |Omega_kj| plus one FP64-level ulp of slack); the sketch of K in FP32
 1e-5 (the Y bar); K^-1 A 1e-5 with FP64 leaves on this well-conditioned simulation (the
-eigenvalues exp(-0.01 i) decay slowly, so the d columns of Y are far from dependent).
+eigenvalues exp(-0.01 i) decay slowly, so the d columns of Y are far from dependent); the
+matrix-free sketch with a dense Omega on the tensor cores max(1e-5, (n / 16) 2^-23), the bound
+of their FP32 accumulation (as for the multi-term forms at full size).
 """
 import numpy as np
 import pytest
@@ -93,5 +95,6 @@ def test_matrix_free_sketch_with_a_dense_omega(ctx, kind):
     ck.check(ctx)
     Yo = osk.sketch(pts.astype(np.float64), 0, 0.15, 1.1, oracle_omega(kind, n, d, 3))
     e = rel(Y, Yo)
-    print("matrix-free sketch, %s Omega: rel err %.2e" % (kind, e))
-    assert e <= 1e-5
+    tol = max(1e-5, (n / 16.0) * 2.0 ** -23)   # the tensor cores' FP32 accumulation (tests/test_gpu_fullsize.py)
+    print("matrix-free sketch, %s Omega: rel err %.2e (bar %.1e)" % (kind, e, tol))
+    assert e <= tol

@@ -60,7 +60,7 @@ SKETCH_CASES = [
     (2085, 512, okk.SE, 0.1, 2),
     (300, 16, okk.MATERN52, 0.3, 1),
 ]
-PREC_TOL = [("fp32", 1e-5), ("bf16", 4e-3), ("bf16x2", 3e-5), ("bf16x3", 1e-5)]
+PREC_TOL = [("fp32", 1e-5), ("bf16", 4e-3), ("bf16x2", 3e-5), ("bf16x3", 1e-5), ("fp32_wht", 1e-5)]
 
 
 @pytest.mark.parametrize("prec,tol", PREC_TOL)
@@ -79,7 +79,7 @@ def test_sketch_matches_oracle(ctx, prec, tol, n, d, kind, ell, dim):
     assert err <= tol
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16", 4e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16", 4e-3), ("fp32_wht", 1e-5)])
 @pytest.mark.parametrize("kind", [okk.SE, okk.MATERN52])
 def test_derivative_sketch_matches_oracle(ctx, prec, tol, kind):
     n, d, dim = 1500, 64, 2

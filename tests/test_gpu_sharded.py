@@ -32,7 +32,7 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp32", "fp32_wht"])
 def test_sketch_rows_are_the_rows_of_the_sketch(ctx, prec):
     n, d = 5000, 128
     pts = torch.from_numpy(synth.points(n, 2, 1)).cuda()
