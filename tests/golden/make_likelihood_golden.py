@@ -7,7 +7,12 @@ variance 1, nugget 1e-4, through the method's K_tilde with a d = 384 sketch (Def
 Sec. 3.2), a TSQR with 2048-row leaves (Sec. 3.3) and one refinement step.  With
 --floor it also writes the same quantities with every kernel entry (and derivative entry)
 rounded to FP32 before the sketch: the floor of a method whose kernel entries carry FP32
-precision.  Usage: python tests/golden/make_likelihood_golden.py [--floor] [--workers N]
+precision - and, from the same sketches, the floor of the library's FP32-level forms at their
+working precision: the sketches Y and Y' rounded to FP32 (the arrays those forms store), the
+leaf Householder factorisations in FP32 and alpha = K_tilde^-1 y rounded to FP32 before the
+gradient.  Usage:
+  python tests/golden/make_likelihood_golden.py [--floor] [--keep-exact] [--workers N]
+(--keep-exact reuses the exact value already stored instead of recomputing it.)
 The sketch row blocks are spread over N processes (default: all CPUs); each block is the
 oracle's own computation.  The record is rewritten after each stage.  Takes tens of minutes
 (two n x n x d sketches in FP64 per stage).
@@ -66,16 +71,29 @@ def sketches(pts, kind, ell, var, O, round32, workers, block=256):
     return Y, Yd
 
 
+def likelihood(cfg, y, O, Y, Yd, working32):
+    """NLL, gradient and log-determinant from the two sketches (one refinement step); with
+    working32 the FP32 storage of the sketches and of alpha and FP32 leaves."""
+    r32 = lambda M: np.asarray(M, dtype=np.float32).astype(np.float64)
+    if working32:
+        Y, Yd = r32(Y), r32(Yd)
+    f = olr.factorise(Y, O, cfg["tau"], cfg["block_rows"], np.float32 if working32 else np.float64)
+    val, alpha = olr.nll(f, y, 1)
+    g, _ = olr.grad(f, y, Y, Yd, r32(alpha) if working32 else alpha)
+    return {"nll": float(val), "grad": [float(x) for x in g], "logdet": float(f.logdet())}
+
+
 def evaluate(cfg, round32, workers):
+    """The exact record (round32 False), or the two floors (round32 True) from one pair of
+    sketches of FP32-rounded entries."""
     n, d = cfg["n"], cfg["d"]
     pts = synth.points(n, cfg["dim"], seed=0).astype(np.float64)
     y = synth.gp_targets(pts, cfg["ell"], cfg["var"], cfg["tau"], seed=0).astype(np.float64)
     O = oom.omega_matrix(n, d, cfg["seed"])
     Y, Yd = sketches(pts, cfg["kind"], cfg["ell"], cfg["var"], O, round32, workers)
-    f = olr.factorise(Y, O, cfg["tau"], cfg["block_rows"])
-    val, alpha = olr.nll(f, y, 1)
-    g, _ = olr.grad(f, y, Y, Yd, alpha)
-    return {"nll": float(val), "grad": [float(x) for x in g], "logdet": float(f.logdet())}
+    if not round32:
+        return likelihood(cfg, y, O, Y, Yd, False)
+    return likelihood(cfg, y, O, Y, Yd, False), likelihood(cfg, y, O, Y, Yd, True)
 
 
 def main():
@@ -93,13 +111,18 @@ def main():
             json.dump(rec, fh, indent=1)
 
     t0 = time.time()
-    rec["exact"] = evaluate(cfg, False, workers)
-    print("exact", rec["exact"], "%.0f s" % (time.time() - t0), flush=True)
-    save()
+    if "--keep-exact" in sys.argv and os.path.exists(OUT):
+        with open(OUT) as fh:
+            rec["exact"] = json.load(fh)["exact"]
+    else:
+        rec["exact"] = evaluate(cfg, False, workers)
+        print("exact", rec["exact"], "%.0f s" % (time.time() - t0), flush=True)
+        save()
     if "--floor" in sys.argv:
         t0 = time.time()
-        rec["fp32_kernel_entries"] = evaluate(cfg, True, workers)
+        rec["fp32_kernel_entries"], rec["fp32_working_precision"] = evaluate(cfg, True, workers)
         print("fp32 entries", rec["fp32_kernel_entries"], "%.0f s" % (time.time() - t0), flush=True)
+        print("fp32 working precision", rec["fp32_working_precision"], flush=True)
         save()
 
 
