@@ -1,0 +1,103 @@
+// A double-FP32 number: the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2,
+// about 48 significand bits with FP32's exponent range.  This part runs FP64 at a small
+// fraction of its FP32 rate, so the R-tree combine, the one place the method needs more
+// than FP32, computes in this type on the FP32 pipes instead (an operation costs 3 to 20
+// FP32 instructions against one FP64 instruction at 1/64 of the rate).
+//
+// The arithmetic is the standard error-free-transformation scheme: Knuth's TwoSum and
+// Dekker's Fast2Sum for additions, the FMA-based exact product for multiplications
+// (Dekker; Hida, Li & Bailey, "Algorithms for quad-double precision floating point
+// arithmetic", 2001, for the double-double operations built from them).  Addition is the
+// accurate variant (both halves summed exactly before renormalising), so cancellation in a
+// dot product costs no more than 2^-44 relative to the operands.  The translation unit must
+// not be compiled with value-changing floating-point flags (reassociation, fast math), which
+// would undo the error-free transformations.
+#ifndef CKINV_DFLOAT_CUH
+#define CKINV_DFLOAT_CUH
+
+#include <cuda_runtime.h>
+
+namespace ckinv {
+// The type and its functions live in their own namespace: argument-dependent lookup finds
+// sqrt and __shfl_xor_sync for dfloat, while the same unqualified calls on float and double
+// in namespace ckinv still find the global ones.
+namespace dd {
+
+struct dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfloat(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ dfloat(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+// s + e = a + b exactly (any magnitudes)
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return dfloat(s, e);
+}
+// s + e = a + b exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ dfloat fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return dfloat(s, b - (s - a));
+}
+
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const dfloat s = two_sum(a.hi, b.hi);
+  const dfloat t = two_sum(a.lo, b.lo);
+  dfloat u = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);              // the exact product's rounding error
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
+  // long division: q1 from the leading halves, then the remainder's quotient as correction
+  const float q1 = a.hi / b.hi;
+  const dfloat r = a - b * dfloat(q1, 0.f);
+  const float q2 = r.hi / b.hi;
+  const dfloat r2 = r - b * dfloat(q2, 0.f);
+  const float q3 = r2.hi / b.hi;
+  const dfloat q = fast_two_sum(q1, q2);
+  return q + dfloat(q3, 0.f);
+}
+
+__device__ __forceinline__ dfloat sqrt(dfloat a) {
+  if (!(a.hi > 0.f)) return dfloat(0.f, 0.f);
+  // one Newton correction of the FP32 root: s + (a - s^2) / (2 s)
+  const float s = sqrtf(a.hi);
+  const dfloat r = a - dfloat(s, 0.f) * dfloat(s, 0.f);
+  return fast_two_sum(s, r.hi / (2.f * s));
+}
+
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
+__device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }
+
+// Comparisons of normalised values: the high halves decide unless equal.
+__device__ __forceinline__ bool operator>(dfloat a, dfloat b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(dfloat a, dfloat b) { return b > a; }
+__device__ __forceinline__ bool operator>=(dfloat a, dfloat b) { return !(b > a); }
+__device__ __forceinline__ bool operator<=(dfloat a, dfloat b) { return !(a > b); }
+
+__device__ __forceinline__ dfloat __shfl_xor_sync(unsigned mask, dfloat v, int lane_mask) {
+  return dfloat(::__shfl_xor_sync(mask, v.hi, lane_mask), ::__shfl_xor_sync(mask, v.lo, lane_mask));
+}
+
+}  // namespace dd
+using dd::dfloat;
+}  // namespace ckinv
+
+#endif

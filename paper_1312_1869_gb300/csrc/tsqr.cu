@@ -17,6 +17,9 @@
 // tree levels hand FP32 copies of their reflectors to an FP32 Q_hat: the combine is where
 // FP64 buys accuracy, and an FP64 product on this part costs ~60x an FP32 one).
 #include "internal.cuh"
+#include "dfloat.cuh"
+
+#include <type_traits>
 
 namespace ckinv {
 namespace {
@@ -273,9 +276,10 @@ __global__ void k_scatter_x(const T *Qs, const int *top, const int *bot, int d, 
 }
 
 // dst = (float) src, n elements.
-__global__ void k_narrow(const double *src, float *dst, int64_t n) {
+template <typename T>
+__global__ void k_narrow(const T *src, float *dst, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = (float)src[e];
+    dst[e] = static_cast<float>(src[e]);
 }
 
 // Q_hat rows of leaf p = Qs_p[0:h_p] (FP32 output, ld n).
@@ -640,8 +644,15 @@ __device__ void sq_tblock_role(T *sm, T *Tm, const T *S, int d, int jq, int r0) 
 // Step q of a level (j0 = q NBS), combine blockIdx.y: CTAs [0, nP) factor panel q, the
 // next nU apply panel q-1 to the columns after panel q, the next nS form S for panel q-1
 // (into buffer (q-1) & 1), the rest form T's blocks for panel q-2 (from buffer q & 1).
+// CTAs of k_sq_step resident per SM: FP64 tiles are short of FP64 units, not registers;
+// double-FP32 ones need twice the registers of FP64 for the same values.
 template <typename T>
-__global__ void __launch_bounds__(SQ_THREADS, sizeof(T) == 8 ? 3 : 1) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
+constexpr int sq_min_blocks() {
+  return std::is_same<T, double>::value ? 3 : std::is_same<T, dfloat>::value ? 2 : 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SQ_THREADS, sq_min_blocks<T>()) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
                                                         int nS, int uw) {
   constexpr int NBS = sq_nb<T>();
   extern __shared__ __align__(16) uint8_t sm_raw[];
@@ -886,17 +897,21 @@ Error assemble_t(const ckinv_ctx *ctx, const Stage<T> &s, int d, int nb0, cudaSt
   return e;
 }
 
+// A combine stage: the panel-by-panel factorization, then its R factors into the slots.
+template <typename T>
+Error factor_stacked(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot, cudaStream_t st, bool with_t) {
+  CK_TRY(sq_factor<T>(ctx, s, d, with_t, st));
+  dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 64), s.P);
+  note_launch();
+  k_extract_r<T><<<g, 256, 0, st>>>(s.M, s.H, d, s.top, Rslot);
+  CK_CUDA(cudaGetLastError());
+  return ok();
+}
+
 template <typename T>
 Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot, cudaStream_t st,
                    bool with_t = true) {
-  if (s.stacked) {
-    CK_TRY(sq_factor<T>(ctx, s, d, with_t, st));
-    dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 64), s.P);
-    note_launch();
-    k_extract_r<T><<<g, 256, 0, st>>>(s.M, s.H, d, s.top, Rslot);
-    CK_CUDA(cudaGetLastError());
-    return ok();
-  }
+  if (s.stacked) return factor_stacked<T>(ctx, s, d, Rslot, st, with_t);
   T *W = nullptr, *W2 = nullptr;
   const size_t sw = (size_t)s.P * ((d / 2 + NB) * (d / 2 + NB));
   CK_CUDA(dev_alloc((void **)&W, sizeof(T) * sw, st));
@@ -988,39 +1003,45 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     // ---- tree stages, bottom-up
     std::vector<Stage<float>> sf(Hn);
     std::vector<Stage<double>> sd(Hn);
+    std::vector<Stage<dfloat>> sx(Hn);
     for (int l = 0; l < Hn && !e.st; ++l) {
       const Level &lv = levels[l];
       const int P = (int)lv.top.size();
       dim3 g((unsigned)std::min<int64_t>(ceil_div(2LL * d * d, 256), 256), P);
-      if (lv.fp64) {
+      if (lv.fp64 && LEAF64) {
+        // FP64 leaves: an FP64 tree, whose reflectors and T factors form an FP64 Q_hat
         if ((e = alloc_stage<double>(sd[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
         sd[l].stacked = true;
         note_launch();
         k_build_stack<double><<<g, 256, 0, st>>>(Rslot, sd[l].top, sd[l].bot, d, sd[l].M);
-        if ((e = factor_stage<double>(ctx, sd[l], d, Rslot, st, LEAF64)).st) break;
-        if (!LEAF64) {
-          // Q_hat is applied in FP32 after FP32 leaves: keep FP32 copies of the level's
-          // reflectors and T factors (the combine itself, and R, stay FP64)
-          Stage<float> &q = sf[l];
-          q.P = P;
-          q.H = 2 * d;
-          q.stacked = true;
-          q.top = sd[l].top;
-          q.bot = sd[l].bot;
-          const int64_t nv = (int64_t)P * 2 * d * d, nt = (int64_t)P * d * d;
-          if (dev_alloc((void **)&q.Vx, sizeof(float) * nv, st) != cudaSuccess ||
-              dev_alloc((void **)&q.Tm, sizeof(float) * nt, st) != cudaSuccess) {
-            e = fail(CKINV_ENOMEM, "tsqr FP32 reflector copies");
-            break;
-          }
-          owned.insert(owned.end(), {(void *)q.Vx, (void *)q.Tm});
-          note_launch();
-          k_narrow<<<(unsigned)std::min<int64_t>(ceil_div(nv, 256), 4096), 256, 0, st>>>(sd[l].Vx, q.Vx, nv);
-          note_launch();
-          k_narrow<<<(unsigned)std::min<int64_t>(ceil_div(nt, 256), 4096), 256, 0, st>>>(sd[l].Tm, q.Tm, nt);
-          // the FP64 combine formed T's diagonal blocks only; the rest in FP32 for Q_hat
-          if ((e = assemble_t<float>(ctx, q, d, sq_nb<double>(), st)).st) break;
+        if ((e = factor_stacked<double>(ctx, sd[l], d, Rslot, st, true)).st) break;
+      } else if (lv.fp64) {
+        // FP32 leaves: the combine in double-FP32 arithmetic (R in and out as FP64); Q_hat
+        // is applied in FP32, so keep FP32 copies of the level's reflectors and T factors
+        if ((e = alloc_stage<dfloat>(sx[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
+        sx[l].stacked = true;
+        note_launch();
+        k_build_stack<dfloat><<<g, 256, 0, st>>>(Rslot, sx[l].top, sx[l].bot, d, sx[l].M);
+        if ((e = factor_stacked<dfloat>(ctx, sx[l], d, Rslot, st, false)).st) break;
+        Stage<float> &q = sf[l];
+        q.P = P;
+        q.H = 2 * d;
+        q.stacked = true;
+        q.top = sx[l].top;
+        q.bot = sx[l].bot;
+        const int64_t nv = (int64_t)P * 2 * d * d, nt = (int64_t)P * d * d;
+        if (dev_alloc((void **)&q.Vx, sizeof(float) * nv, st) != cudaSuccess ||
+            dev_alloc((void **)&q.Tm, sizeof(float) * nt, st) != cudaSuccess) {
+          e = fail(CKINV_ENOMEM, "tsqr FP32 reflector copies");
+          break;
         }
+        owned.insert(owned.end(), {(void *)q.Vx, (void *)q.Tm});
+        note_launch();
+        k_narrow<dfloat><<<(unsigned)std::min<int64_t>(ceil_div(nv, 256), 4096), 256, 0, st>>>(sx[l].Vx, q.Vx, nv);
+        note_launch();
+        k_narrow<dfloat><<<(unsigned)std::min<int64_t>(ceil_div(nt, 256), 4096), 256, 0, st>>>(sx[l].Tm, q.Tm, nt);
+        // the combine formed T's diagonal blocks only; the rest in FP32 for Q_hat
+        if ((e = assemble_t<float>(ctx, q, d, sq_nb<dfloat>(), st)).st) break;
       } else {
         if ((e = alloc_stage<float>(sf[l], P, 2 * d, d, lv.top, lv.bot, ctx, owned, st)).st) break;
         sf[l].stacked = true;

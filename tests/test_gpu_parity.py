@@ -147,6 +147,34 @@ def test_tsqr_matches_oracle(ctx, n, d, b, f64, leaf64):
     assert np.abs(Q.T @ Q - np.eye(d)).max() <= (1e-6 if leaf64 else 1e-5)
 
 
+@pytest.mark.parametrize("f64,bar", [(-1, 1e-11), (2, None), (0, None)])
+def test_tree_combine_precision(ctx, f64, bar):
+    """The precision of the R-tree combine alone.  Every leaf block of Y is already upper
+    triangular (zero below its first d rows), so the leaves' Householder QR reflects nothing
+    and hands the tree its blocks exactly; the final R's error is then the tree's own.  With
+    every level combined in the FP64-class arithmetic (double-FP32, ~2^-47 per operation)
+    R must match the oracle's FP64 TSQR to 1e-11; with FP32 levels it cannot (printed: the
+    test shows that the bar separates the two)."""
+    L, d, b = 16, 128, 512
+    rng = np.random.default_rng(77)
+    Y = np.zeros((L * b, d), np.float32)
+    for i in range(L):
+        Ri = np.triu(rng.standard_normal((d, d))) + np.diag(3.0 + np.abs(rng.standard_normal(d)))
+        Y[i * b:i * b + d] = Ri.astype(np.float32)
+    plan = ck.Plan(n=L * b, d=d, block_rows=b, seed=1, tree_fp64_levels=f64, leaf_fp64=0)
+    f = ck.tsqr(ctx, plan, ck.Kernel(ck.SE, 1, 1, 1e-3), col(Y))
+    R = host(f.r())
+    torch.cuda.synchronize()
+    ck.check(ctx)
+    Ro = ots.tsqr(Y.astype(np.float64), b)["R"]
+    err = rel(R, Ro)
+    print("tree combine, %s FP64-class levels: R err %.3e" % ("all" if f64 < 0 else f64, err))
+    if bar is not None:
+        assert err <= bar
+    else:
+        assert err > 1e-9        # FP32 levels: the bar above would catch an FP32 combine
+
+
 @pytest.mark.parametrize("n,d,b,f64", [(20000, 128, 1024, 1), (9000, 512, 2048, 1), (65536, 128, 1024, -1),
                                        (32768, 512, 2048, -1)])
 def test_tsqr_bf16_forms_tensor_core_gemms(ctx, n, d, b, f64):
