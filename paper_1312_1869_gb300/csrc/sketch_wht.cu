@@ -35,12 +35,15 @@ constexpr int kWMaxU = 16;            // output slots per lane: d <= 512
 constexpr int kWPad = 33;             // padded row of the transpose buffers
 
 // The points past n (the padding of K0 to order N) have zero kernel entries.  For the
-// squared-exponential kernel itself they are placed at +infinity in every coordinate: their
-// squared distance to any finite point is +infinity, whose exp2(-inf) is exactly 0, so the hot
-// loop needs no mask.  The other kernels (the derivative, whose factor r^2 would make that
-// inf * 0, and Matern-5/2, whose polynomial in r does the same) mask the last chunk's entries.
+// squared-exponential kernel they are placed at +infinity in every coordinate: their squared
+// distance to any finite point is +infinity, whose exp2(-inf) is exactly 0, so the hot loop
+// needs no mask.  The derivative's factor r^2 would make that inf * 0, so its scaled squared
+// distance is first clamped at 1e4, which changes no entry (exp2(-x) is exactly 0 in FP32 for
+// every x above ~150).  Matern-5/2, whose polynomial in r would overflow the same way at any
+// clamp that is exact for every lengthscale, masks the last chunk's entries instead.
 constexpr float kPadFar = __builtin_huge_valf();
-__host__ __device__ constexpr bool pad_far(int kind, bool deriv) { return kind == CKINV_SE && !deriv; }
+constexpr float kSeClamp = 1e4f;
+__host__ __device__ constexpr bool pad_far(int kind, bool) { return kind == CKINV_SE; }
 
 // Shared memory of one CTA.  The transpose buffers double, after the last chunk, as the
 // d x ROWS staging tile of the output (column stride ROWS + 1).
@@ -138,6 +141,7 @@ __device__ __forceinline__ void eval_rows(const float *P, int dim, const float (
         const float dz = x[r][2] - q2;
         r2 = fmaf(dz, dz, r2);
       }
+      if (DERIV && KIND == CKINV_SE) r2 = fminf(r2, kSeClamp);
       float e = dev::kernel_value(KIND, r2, inv_l, DERIV);
       if (TAIL) e = kb < rem ? e : 0.f;
       v[r][t] = flip_if(e, smask, t);
@@ -148,21 +152,22 @@ __device__ __forceinline__ void eval_rows(const float *P, int dim, const float (
 // rows (0, 1, ..., R-1) -> (S, S+1, ..., S-1) of the accumulators and coordinates
 template <int R, int S>
 __device__ __forceinline__ void rotate_rows(float (&acc)[R][kWMaxU], float (&xr)[R][3]) {
-  if (S % R == 0) return;
-  float ta[R][kWMaxU], tx[R][3];
+  if constexpr (S % R != 0) {
+    float ta[R][kWMaxU], tx[R][3];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
-    for (int u = 0; u < kWMaxU; ++u) ta[r][u] = acc[(r + S) % R][u];
+      for (int u = 0; u < kWMaxU; ++u) ta[r][u] = acc[(r + S) % R][u];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) tx[r][c] = xr[(r + S) % R][c];
-  }
+      for (int c = 0; c < 3; ++c) tx[r][c] = xr[(r + S) % R][c];
+    }
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < R; ++r) {
 #pragma unroll
-    for (int u = 0; u < kWMaxU; ++u) acc[r][u] = ta[r][u];
+      for (int u = 0; u < kWMaxU; ++u) acc[r][u] = ta[r][u];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) xr[r][c] = tx[r][c];
+      for (int c = 0; c < 3; ++c) xr[r][c] = tx[r][c];
+    }
   }
 }
 
