@@ -229,6 +229,19 @@ struct TsqrOut {
 };
 Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
                   const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st);
+// One problem of a joint factorization: Y (n x d, ld ldy) -> Q_hat (ld ldq) and R (d x d).
+struct TsqrProblem {
+  int64_t n;
+  const float *Y;
+  int64_t ldy;
+  float *Q;
+  int64_t ldq;
+  double *R;
+};
+// Several problems of the same d factored together (one leaf stage and one stage per tree
+// level for all of them); each problem's results are those of its own factorization.
+Error tsqr_factor_multi(ckinv_ctx *ctx, const std::vector<TsqrProblem> &probs, int d, int b, int fp64_levels,
+                        bool leaf_fp64, bool tc_gemm, cudaStream_t st);
 int auto_block_rows(int64_t n, int d, int sm_count);
 // Tallest TSQR leaf (a multiple of 16) whose panels fit in shared memory at this d.
 int max_leaf_rows(int d, bool leaf_fp64);

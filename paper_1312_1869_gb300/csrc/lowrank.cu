@@ -441,6 +441,18 @@ __device__ __forceinline__ void slot_set(double (&v)[kSolveSlots], int s, double
 #pragma unroll
   for (int t = 0; t < kSolveSlots; ++t) v[t] = (t == s) ? x : v[t];
 }
+template <int R>
+__device__ __forceinline__ double slot_get_r(const double (&v)[kSolveSlots][R], int s, int r) {
+  double x = 0.0;
+#pragma unroll
+  for (int t = 0; t < kSolveSlots; ++t) x = (t == s) ? v[t][r] : x;
+  return x;
+}
+template <int R>
+__device__ __forceinline__ void slot_set_r(double (&v)[kSolveSlots][R], int s, int r, double x) {
+#pragma unroll
+  for (int t = 0; t < kSolveSlots; ++t) v[t][r] = (t == s) ? x : v[t][r];
+}
 __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
                "l"(src)
@@ -452,15 +464,17 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double *__restrict__ LU,
+template <int R>
+__global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, int m, const double *__restrict__ LU,
                                                             const int32_t *__restrict__ piv, double *X, int trans) {
   extern __shared__ __align__(16) double sm[];
   const int bufsz = kSolveLdT * d;
-  double *xs = sm + 2 * (size_t)bufsz;                 // the vector, for the interchanges
-  double *xc = xs + d;                                 // two chunks of solved unknowns
-  int32_t *ps = reinterpret_cast<int32_t *>(xc + 2 * kSolveChunk);
+  double *xs = sm + 2 * (size_t)bufsz;                 // R vectors, for the interchanges
+  double *xc = xs + (size_t)R * d;                     // two chunks of solved unknowns per vector
+  int32_t *ps = reinterpret_cast<int32_t *>(xc + 2 * R * kSolveChunk);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double *x = X + (int64_t)blockIdx.x * d;
+  const int c0 = blockIdx.x * R;                       // this block's first right-hand side
+  const int nr = min(R, m - c0);
   const int nchunk = (d + kSolveChunk - 1) / kSolveChunk;
   // chunk-steps 0 .. 2 nchunk - 1: the first pass ascends (forward), the second descends
   auto chunk_of = [&](int k) { return k < nchunk ? k : 2 * nchunk - 1 - k; };
@@ -484,23 +498,24 @@ __global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double 
     cp_async_commit();
   };
   issue(0);
-  for (int i = tid; i < d; i += kSolveThreads) {
-    ps[i] = piv[i];
-    xs[i] = x[i];
-  }
+  for (int i = tid; i < d; i += kSolveThreads) ps[i] = piv[i];
+  for (int r = 0; r < R; ++r)
+    for (int i = tid; i < d; i += kSolveThreads) xs[(size_t)r * d + i] = r < nr ? X[(int64_t)(c0 + r) * d + i] : 0.0;
   __syncthreads();
-  if (!trans && tid == 0) {
+  if (!trans && tid < R) {
+    double *xr = xs + (size_t)tid * d;
     for (int j = 0; j < d; ++j) {
       const int p = ps[j];
-      if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+      if (p != j) { double t = xr[j]; xr[j] = xr[p]; xr[p] = t; }
     }
   }
   __syncthreads();
-  double v[kSolveSlots], rd[kSolveSlots];
+  double v[kSolveSlots][R], rd[kSolveSlots];
 #pragma unroll
   for (int s = 0; s < kSolveSlots; ++s) {
     const int i = s * kSolveThreads + tid;
-    v[s] = i < d ? xs[i] : 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[s][r] = i < d ? xs[(size_t)r * d + i] : 0.0;
     rd[s] = i < d ? 1.0 / LU[(int64_t)i * d + i] : 0.0;
   }
   for (int k = 0; k < 2 * nchunk; ++k) {
@@ -520,23 +535,33 @@ __global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double 
     const bool unit = trans ? !fwd : fwd;      // L and L^T have a unit diagonal
     const int j0 = chunk_of(k) * kSolveChunk;
     const int w = min(kSolveChunk, d - j0);
-    double *xck = xc + (k & 1) * kSolveChunk;
-    // 1. diagonal block, by the warp that owns rows j0 .. j0+w (all in one slot)
+    double *xck = xc + (k & 1) * R * kSolveChunk;
+    // 1. diagonal block, by the warp that owns rows j0 .. j0+w (all in one slot); the
+    // vectors' substitutions are independent chains, interleaved
     if (warp == ((j0 % kSolveThreads) >> 5)) {
       const int q0 = j0 / kSolveThreads;
       const int i = q0 * kSolveThreads + tid;
-      double vq = slot_get(v, q0);
+      double vq[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) vq[r] = slot_get_r<R>(v, q0, r);
       const double rq = slot_get(rd, q0);
       const bool mine = i >= j0 && i < j0 + w;
       for (int t = 0; t < w; ++t) {
         const int jj = fwd ? t : w - 1 - t;
         const int j = j0 + jj;
-        if (!unit && i == j) vq *= rq;
-        const double xj = __shfl_sync(0xffffffffu, vq, j & 31);
-        if (mine && (fwd ? i > j : i < j)) vq = fma(-opA(i, jj), xj, vq);
+        const double a = (mine && (fwd ? i > j : i < j)) ? opA(i, jj) : 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (!unit && i == j) vq[r] *= rq;
+          const double xj = __shfl_sync(0xffffffffu, vq[r], j & 31);
+          if (mine && (fwd ? i > j : i < j)) vq[r] = fma(-a, xj, vq[r]);
+        }
       }
-      slot_set(v, q0, vq);
-      if (mine) xck[i - j0] = vq;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        slot_set_r<R>(v, q0, r, vq[r]);
+        if (mine) xck[r * kSolveChunk + (i - j0)] = vq[r];
+      }
     }
     __syncthreads();
     // 2. the chunk applied to the rows still to be solved
@@ -544,20 +569,24 @@ __global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double 
     for (int s = 0; s < kSolveSlots; ++s) {
       const int i = s * kSolveThreads + tid;
       if (fwd ? (i >= j0 + w && i < d) : (i < j0)) {
-        double a = v[s];
-        if (w == kSolveChunk) {
 #pragma unroll
-          for (int t = 0; t < kSolveChunk; ++t) {
-            const int jj = fwd ? t : kSolveChunk - 1 - t;
-            a = fma(-opA(i, jj), xck[jj], a);
+        for (int r = 0; r < R; ++r) {
+          double a = v[s][r];
+          const double *xr = xck + r * kSolveChunk;
+          if (w == kSolveChunk) {
+#pragma unroll
+            for (int t = 0; t < kSolveChunk; ++t) {
+              const int jj = fwd ? t : kSolveChunk - 1 - t;
+              a = fma(-opA(i, jj), xr[jj], a);
+            }
+          } else {
+            for (int t = 0; t < w; ++t) {
+              const int jj = fwd ? t : w - 1 - t;
+              a = fma(-opA(i, jj), xr[jj], a);
+            }
           }
-        } else {
-          for (int t = 0; t < w; ++t) {
-            const int jj = fwd ? t : w - 1 - t;
-            a = fma(-opA(i, jj), xck[jj], a);
-          }
+          v[s][r] = a;
         }
-        v[s] = a;
       }
     }
     __syncthreads();                                   // buffer k & 1 is refilled at step k + 2
@@ -566,28 +595,35 @@ __global__ void __launch_bounds__(kSolveThreads) k_lu_solve(int d, const double 
 #pragma unroll
     for (int s = 0; s < kSolveSlots; ++s) {
       const int i = s * kSolveThreads + tid;
-      if (i < d) x[i] = v[s];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i < d && r < nr) X[(int64_t)(c0 + r) * d + i] = v[s][r];
     }
   } else {
 #pragma unroll
     for (int s = 0; s < kSolveSlots; ++s) {
       const int i = s * kSolveThreads + tid;
-      if (i < d) xs[i] = v[s];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (i < d) xs[(size_t)r * d + i] = v[s][r];
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < R) {
+      double *xr = xs + (size_t)tid * d;
       for (int j = d - 1; j >= 0; --j) {
         const int p = ps[j];
-        if (p != j) { double t = xs[j]; xs[j] = xs[p]; xs[p] = t; }
+        if (p != j) { double t = xr[j]; xr[j] = xr[p]; xr[p] = t; }
       }
     }
     __syncthreads();
-    for (int i = tid; i < d; i += kSolveThreads) x[i] = xs[i];
+    for (int r = 0; r < nr; ++r)
+      for (int i = tid; i < d; i += kSolveThreads) X[(int64_t)(c0 + r) * d + i] = xs[(size_t)r * d + i];
   }
 }
 
-static size_t lu_solve_smem(int d) {
-  return sizeof(double) * ((size_t)2 * kSolveLdT * d + d + 2 * kSolveChunk) + sizeof(int32_t) * (size_t)d;
+static size_t lu_solve_smem(int d, int R) {
+  return sizeof(double) * ((size_t)2 * kSolveLdT * d + (size_t)R * d + 2 * (size_t)R * kSolveChunk) +
+         sizeof(int32_t) * (size_t)d;
 }
 
 // C (d x m) = op(A) (d x d) * Bm (d x m), FP64, ld = d.  transA: C = A^T B.
@@ -768,12 +804,25 @@ Error lu_factor_f64(ckinv_ctx *ctx, int n, double *A, int32_t *piv, double *loga
   return lu_blocked(ctx, 1, n, A, piv, logabsdet, st);
 }
 
+// Right-hand sides per block: one for a vector or a few columns (the latency of the
+// substitution chain sets the time); four for a matrix of many columns, where one column per
+// block would fill every SM with blocks that each stage the whole factor and keep the FP64
+// units a quarter busy.  A column's operations are the same whatever the grouping.
 static Error lu_solve(int d, int m, const double *LU, const int32_t *piv, double *X, int trans, cudaStream_t st) {
   if (d > kSolveThreads * kSolveSlots) return fail(CKINV_EUNSUPPORTED, "triangular solve: d above 512");
   if (m <= 0 || d <= 0) return ok();
-  CK_CUDA(cudaFuncSetAttribute(k_lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)lu_solve_smem(kSolveThreads * kSolveSlots)));
-  ::ckinv::note_launch(), k_lu_solve<<<(unsigned)m, kSolveThreads, lu_solve_smem(d), st>>>(d, LU, piv, X, trans);
+  const int R = m >= 64 ? 4 : 1;
+  const size_t smem = lu_solve_smem(d, R);
+  if (R == 4) {
+    CK_CUDA(cudaFuncSetAttribute(k_lu_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lu_solve_smem(kSolveThreads * kSolveSlots, 4)));
+    ::ckinv::note_launch(),
+        k_lu_solve<4><<<(unsigned)ceil_div(m, 4), kSolveThreads, smem, st>>>(d, m, LU, piv, X, trans);
+  } else {
+    CK_CUDA(cudaFuncSetAttribute(k_lu_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lu_solve_smem(kSolveThreads * kSolveSlots, 1)));
+    ::ckinv::note_launch(), k_lu_solve<1><<<(unsigned)m, kSolveThreads, smem, st>>>(d, m, LU, piv, X, trans);
+  }
   CK_CUDA(cudaGetLastError());
   return ok();
 }

@@ -199,16 +199,17 @@ __global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, 
   }
 }
 
-// Leaf blocks of Y (FP32, ld ldy) into the stage matrix (H x d per leaf), zero-padded.
+// Leaf blocks into the stage matrix (H x d per leaf), zero-padded: leaf p's rows start at
+// src[p] (FP32, column-major, ld ld[p]; leaves of several problems may share a stage).
 template <typename T>
-__global__ void k_gather_leaves(const float *Y, int64_t ldy, const int64_t *row0, const int *rows, int H, int d,
-                                T *M) {
+__global__ void k_gather_leaves(const float *const *srcs, const int64_t *ld, const int *rows, int H, int d, T *M) {
   const int p = blockIdx.y;
-  const int64_t r0 = row0[p];
+  const float *Yp = srcs[p];
+  const int64_t ldp = ld[p];
   const int h = rows[p];
   T *dst = M + (int64_t)p * H * d;
   for (int c = blockIdx.x; c < d; c += gridDim.x) {
-    const float *src = Y + r0 + (int64_t)c * ldy;
+    const float *src = Yp + (int64_t)c * ldp;
     T *out = dst + (int64_t)c * H;
     for (int r = threadIdx.x; r < H; r += blockDim.x) out[r] = (r < h) ? (T)src[r] : T(0);
   }
@@ -282,15 +283,15 @@ __global__ void k_narrow(const T *src, float *dst, int64_t n) {
     dst[e] = static_cast<float>(src[e]);
 }
 
-// Q_hat rows of leaf p = Qs_p[0:h_p] (FP32 output, ld n).
+// Q_hat rows of leaf p = Qs_p[0:h_p], to dst[p] (FP32, column-major, ld ld[p]).
 template <typename T>
-__global__ void k_leaf_q(const T *Qs, int H, int d, const int64_t *row0, const int *rows, float *Q, int64_t ldq) {
+__global__ void k_leaf_q(const T *Qs, int H, int d, float *const *dsts, const int64_t *ld, const int *rows) {
   const int p = blockIdx.y;
   const int h = rows[p];
   const T *src = Qs + (int64_t)p * H * d;
   for (int c = blockIdx.x; c < d; c += gridDim.x) {
     const T *in = src + (int64_t)c * H;
-    float *out = Q + row0[p] + (int64_t)c * ldq;
+    float *out = dsts[p] + (int64_t)c * ld[p];
     for (int r = threadIdx.x; r < h; r += blockDim.x) out[r] = (float)in[r];
   }
 }
@@ -927,34 +928,59 @@ Error factor_stage(const ckinv_ctx *ctx, const Stage<T> &s, int d, double *Rslot
   return ok();
 }
 
+// Several independent problems of the same width d factor together: their leaves form one
+// leaf stage, and level l of every problem's tree (counted from its leaves) one combine stage,
+// so each launch covers all problems.  A problem's arithmetic does not depend on the others:
+// every leaf and combine is its own QR (the GEMMs' split of the K dimension may differ with
+// the batch size, which changes rounding only).
 template <typename TL>
-Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const float *Y, int64_t ldy, float *Qout,
-                double *Rout, cudaStream_t st) {
+Error tsqr_impl(ckinv_ctx *ctx, const std::vector<TsqrProblem> &probs, int d, int b, int fp64_levels,
+                cudaStream_t st) {
   constexpr bool LEAF64 = sizeof(TL) == 8;
-  // ---- leaves (Eq. 1)
-  std::vector<int64_t> row0;
+  // ---- leaves (Eq. 1), problem by problem
+  std::vector<const float *> lsrc;
+  std::vector<float *> ldst;
+  std::vector<int64_t> lld, lldq;
   std::vector<int> rows;
-  for (int64_t s0 = 0; s0 < n; s0 += b) {
-    row0.push_back(s0);
-    rows.push_back((int)std::min<int64_t>(b, n - s0));
+  std::vector<int> first(probs.size() + 1, 0);
+  for (size_t q = 0; q < probs.size(); ++q) {
+    const TsqrProblem &pr = probs[q];
+    first[q] = (int)rows.size();
+    std::vector<int64_t> r0;
+    std::vector<int> h;
+    for (int64_t s0 = 0; s0 < pr.n; s0 += b) {
+      r0.push_back(s0);
+      h.push_back((int)std::min<int64_t>(b, pr.n - s0));
+    }
+    if (h.size() > 1 && h.back() < d) {
+      int last = h.back();
+      h.pop_back();
+      r0.pop_back();
+      h.back() += last;
+    }
+    for (size_t i = 0; i < h.size(); ++i) {
+      lsrc.push_back(pr.Y + r0[i]);
+      lld.push_back(pr.ldy);
+      ldst.push_back(pr.Q + r0[i]);
+      lldq.push_back(pr.ldq);
+      rows.push_back(h[i]);
+    }
   }
-  if (rows.size() > 1 && rows.back() < d) {
-    int last = rows.back();
-    rows.pop_back();
-    row0.pop_back();
-    rows.back() += last;
-  }
+  first[probs.size()] = (int)rows.size();
   const int L = (int)rows.size();
   int Hl = 0;
   for (int m : rows) Hl = std::max(Hl, m);
   Hl = (int)ceil_div(Hl, 16) * 16;
   if (panel_smem<TL>(Hl) > kPanelSmemMax)
     return fail(CKINV_EUNSUPPORTED, "tsqr: leaf height too large for the shared-memory panel");
-  // ---- tree levels (Eqs. 2-3)
+  // ---- tree levels (Eqs. 2-3): each problem's binary tree over its own leaves; level l of
+  // all problems is one stage.  The top fp64_levels of a problem's tree are FP64-class.
   std::vector<Level> levels;
-  {
-    std::vector<int> active(L);
-    for (int i = 0; i < L; ++i) active[i] = i;
+  std::vector<int> root(probs.size());
+  for (size_t q = 0; q < probs.size(); ++q) {
+    std::vector<int> active;
+    for (int i = first[q]; i < first[q + 1]; ++i) active.push_back(i);
+    std::vector<Level> own;
     while (active.size() > 1) {
       Level lv;
       std::vector<int> nxt;
@@ -965,29 +991,48 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
       }
       if (active.size() % 2) nxt.push_back(active.back());
       active = nxt;
-      levels.push_back(lv);
+      own.push_back(lv);
+    }
+    root[q] = active[0];
+    const int Hq = (int)own.size();
+    int nf64 = (fp64_levels < 0) ? Hq : std::min(fp64_levels, Hq);
+    if (LEAF64) nf64 = Hq;   // an FP64 leaf stage feeds an all-FP64 tree
+    if (levels.size() < own.size()) levels.resize(own.size());
+    for (int l = 0; l < Hq; ++l) {
+      const bool f64 = l >= Hq - nf64;
+      if (!levels[l].top.empty() && levels[l].fp64 != f64)
+        return fail(CKINV_EINVAL, "tsqr: problems of one factorization need the same FP64-class levels");
+      levels[l].fp64 = f64;
+      levels[l].top.insert(levels[l].top.end(), own[l].top.begin(), own[l].top.end());
+      levels[l].bot.insert(levels[l].bot.end(), own[l].bot.begin(), own[l].bot.end());
     }
   }
   const int Hn = (int)levels.size();
-  int nf64 = (fp64_levels < 0) ? Hn : std::min(fp64_levels, Hn);
-  if (LEAF64) nf64 = Hn;   // an FP64 leaf stage feeds an all-FP64 tree
-  for (int l = 0; l < Hn; ++l) levels[l].fp64 = (l >= Hn - nf64);
 
   std::vector<void *> owned;
   double *Rslot = nullptr, *Xslot = nullptr;
-  int64_t *d_row0 = nullptr;
+  const float **d_src = nullptr;
+  float **d_dst = nullptr;
+  int64_t *d_ld = nullptr, *d_ldq = nullptr;
   int *d_rows = nullptr;
   Error e = ok();
   do {
     if (dev_alloc((void **)&Rslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
         dev_alloc((void **)&Xslot, sizeof(double) * (size_t)L * d * d, st) != cudaSuccess ||
-        dev_alloc((void **)&d_row0, sizeof(int64_t) * L, st) != cudaSuccess ||
+        dev_alloc((void **)&d_src, sizeof(float *) * L, st) != cudaSuccess ||
+        dev_alloc((void **)&d_dst, sizeof(float *) * L, st) != cudaSuccess ||
+        dev_alloc((void **)&d_ld, sizeof(int64_t) * L, st) != cudaSuccess ||
+        dev_alloc((void **)&d_ldq, sizeof(int64_t) * L, st) != cudaSuccess ||
         dev_alloc((void **)&d_rows, sizeof(int) * L, st) != cudaSuccess) {
       e = fail(CKINV_ENOMEM, "tsqr workspace");
       break;
     }
-    owned.insert(owned.end(), {(void *)Rslot, (void *)Xslot, (void *)d_row0, (void *)d_rows});
-    if ((e = stage_upload(ctx, row0.data(), sizeof(int64_t) * L, d_row0, st)).st) break;
+    owned.insert(owned.end(), {(void *)Rslot, (void *)Xslot, (void *)d_src, (void *)d_dst, (void *)d_ld,
+                               (void *)d_ldq, (void *)d_rows});
+    if ((e = stage_upload(ctx, lsrc.data(), sizeof(float *) * L, d_src, st)).st) break;
+    if ((e = stage_upload(ctx, ldst.data(), sizeof(float *) * L, d_dst, st)).st) break;
+    if ((e = stage_upload(ctx, lld.data(), sizeof(int64_t) * L, d_ld, st)).st) break;
+    if ((e = stage_upload(ctx, lldq.data(), sizeof(int64_t) * L, d_ldq, st)).st) break;
     if ((e = stage_upload(ctx, rows.data(), sizeof(int) * L, d_rows, st)).st) break;
     // ---- leaf stage
     Stage<TL> leaf;
@@ -997,7 +1042,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     {
       dim3 g((unsigned)std::min(d, 128), L);
       note_launch();
-      k_gather_leaves<TL><<<g, 256, 0, st>>>(Y, ldy, d_row0, d_rows, Hl, d, leaf.M);
+      k_gather_leaves<TL><<<g, 256, 0, st>>>(d_src, d_ld, d_rows, Hl, d, leaf.M);
     }
     if ((e = factor_stage<TL>(ctx, leaf, d, Rslot, st)).st) break;
     // ---- tree stages, bottom-up
@@ -1051,10 +1096,13 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
       }
     }
     if (e.st) break;
-    // ---- root (Eq. 4): R = D R_root, X_root = D
-    note_launch();
-    k_finish_root<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 256), 256, 0, st>>>(Rslot, d, Rout,
-                                                                                                   Xslot);
+    // ---- each problem's root (Eq. 4): R = D R_root, X_root = D
+    for (size_t q = 0; q < probs.size(); ++q) {
+      const int64_t o = (int64_t)root[q] * d * d;
+      note_launch();
+      k_finish_root<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 256), 256, 0, st>>>(
+          Rslot + o, d, probs[q].R, Xslot + o);
+    }
     // ---- Q_hat, top-down
     const size_t qmax = std::max((size_t)L * Hl * d, (size_t)L * 2 * d * d);
     const size_t zmax = (size_t)L * d * d;
@@ -1084,7 +1132,7 @@ Error tsqr_impl(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, const 
     {
       dim3 g((unsigned)std::min(d, 128), L);
       note_launch();
-      k_leaf_q<TL><<<g, 256, 0, st>>>((TL *)Qs, Hl, d, d_row0, d_rows, Qout, n);
+      k_leaf_q<TL><<<g, 256, 0, st>>>((TL *)Qs, Hl, d, d_dst, d_ldq, d_rows);
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
@@ -1115,8 +1163,8 @@ int auto_block_rows(int64_t n, int d, int sm_count) {
   return (int)b;
 }
 
-Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
-                  const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st) {
+Error tsqr_factor_multi(ckinv_ctx *ctx, const std::vector<TsqrProblem> &probs, int d, int b, int fp64_levels,
+                        bool leaf_fp64, bool tc_gemm, cudaStream_t st) {
   // the FP32 GEMMs of this factorization on the tensor cores or on the CUDA cores
   struct Restore {
     ckinv_ctx *c;
@@ -1124,12 +1172,22 @@ Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool
     ~Restore() { c->gemm_tc = v; }
   } restore{ctx, ctx->gemm_tc};
   ctx->gemm_tc = tc_gemm;
+  if (probs.empty()) return ok();
   if (d % NB != 0) return fail(CKINV_EINVAL, "tsqr: d must be a multiple of 16");
+  for (const TsqrProblem &pr : probs)
+    if (pr.n < d || !pr.Y || !pr.Q || !pr.R || pr.ldy < pr.n || pr.ldq < pr.n)
+      return fail(CKINV_EINVAL, "tsqr: each problem needs n >= d, ld >= n and its buffers");
   const int bmax = max_block_rows(d, leaf_fp64);
   if (bmax < d) return fail(CKINV_EUNSUPPORTED, "tsqr: d too large for a shared-memory panel");
   if (b > bmax) b = bmax;   // R and Q_hat do not depend on the leaf height
-  if (leaf_fp64) return tsqr_impl<double>(ctx, n, d, b, fp64_levels, Y, ldy, Qout, Rout, st);
-  return tsqr_impl<float>(ctx, n, d, b, fp64_levels, Y, ldy, Qout, Rout, st);
+  if (leaf_fp64) return tsqr_impl<double>(ctx, probs, d, b, fp64_levels, st);
+  return tsqr_impl<float>(ctx, probs, d, b, fp64_levels, st);
+}
+
+Error tsqr_factor(ckinv_ctx *ctx, int64_t n, int d, int b, int fp64_levels, bool leaf_fp64, bool tc_gemm,
+                  const float *Y, int64_t ldy, float *Qout, double *Rout, cudaStream_t st) {
+  const TsqrProblem pr{n, Y, ldy, Qout, n, Rout};
+  return tsqr_factor_multi(ctx, std::vector<TsqrProblem>{pr}, d, b, fp64_levels, leaf_fp64, tc_gemm, st);
 }
 
 // The top of a TSQR whose leaves were factored elsewhere (row shards, one per GPU): the
