@@ -636,6 +636,22 @@ def run_ours(args, rank, world, local_rank):
             ck.check(ctx)
             forms[name] = {"solves_per_s": 1e3 / best, "ms_per_solve": best, "tree_fp64_levels": lv,
                            "true_residual_sampled": true_residual(X, A_np, pts_np, cfg, rows)}
+            if prec == "fp32_wht":
+                # the fast-transform sketch alone (CUDA events, best of 3 after the runs above):
+                # n^2 kernel entries, each evaluated, transformed and gathered in FP32
+                sk = None
+                for _ in range(3):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ck.sketch(ctx, plan2, kern, pts, Y=Y)
+                    e1.record(stream)
+                    e1.synchronize()
+                    t = e0.elapsed_time(e1)
+                    sk = t if sk is None else min(sk, t)
+                forms[name]["sketch_ms"] = sk
+                forms[name]["kernel_evals_per_s"] = float(n) * float(n) / (sk / 1e3)
+                forms[name]["sketch_rel_err_sampled"] = sampled_sketch_error(ck, Y, pts_np, cfg, 5, rows)
         forms["residual_note"] = ("||(K0 + tau I) X - A|| / ||A|| on 48 sampled rows, K0 rows from the FP64 oracle: "
                                   "the method's approximation K_tilde of K0 + tau I, not the arithmetic, sets it")
 
