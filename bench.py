@@ -304,8 +304,9 @@ def run_materialised(ck, ctx, dev, stream, peaks):
     """The plain method with K in HBM: n = 65536 points in [0, 1]^3, Matern-5/2 l = 0.15,
     d = 256.  K0 (17.2 GB FP32) is materialised by the library (untimed), then the sketch of
     the given matrix is timed with CUDA events (K read once: the HBM-bound step), in the FP32
-    SIMT form and the one- and three-term tensor-core forms, and the whole solve (sketch, TSQR,
-    core, refined solve of m = 16 right-hand sides) in the form the workload names (FP32)."""
+    SIMT form, the one- and three-term tensor-core forms and the FP32 fast transform over K's
+    columns, and the whole solve (sketch, TSQR, core, refined solve of m = 16 right-hand sides)
+    in the FP32 forms the workload names (SIMT contraction and fast transform)."""
     import torch
     cfg = workload_config("c2_dense_n65536")
     n, d, dim, m = cfg["n"], cfg["d"], cfg["dim"], cfg["m"]
@@ -323,7 +324,7 @@ def run_materialised(ck, ctx, dev, stream, peaks):
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     out = {"workload": "c2_dense_n65536", "n": n, "d": d, "m": m, "K_bytes": bytes_k,
            "timing": "CUDA events on the launching stream, best of 3 after one untimed run"}
-    for name, prec in [("fp32", ck.FP32), ("bf16", ck.BF16), ("bf16x3", ck.BF16X3)]:
+    for name, prec in [("fp32", ck.FP32), ("bf16", ck.BF16), ("bf16x3", ck.BF16X3), ("fp32_wht", ck.FP32_WHT)]:
         p2 = ck.Plan(n=n, d=d, dim=dim, block_rows=cfg["block_rows"], prec=prec, seed=0, refine_steps=1)
         best = None
         for r in range(4):
@@ -341,22 +342,27 @@ def run_materialised(ck, ctx, dev, stream, peaks):
     rows = np.linspace(0, n - 1, 48).astype(np.int64)
     out["sketch_fp32"]["rel_err_sampled"] = sampled_sketch_error(ck, Y_of(ck, ctx, plan, dense, K, Y), pts_np, cfg, 0,
                                                                   rows)
-    best = None
-    for r in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ck.sketch(ctx, plan, dense, K=K, Y=Y)
-        f = ck.tsqr(ctx, plan, dense, Y)
-        ck.solve(ctx, f, A, X)
-        f.free()
-        e1.record(stream)
-        e1.synchronize()
-        if r:
-            t = e0.elapsed_time(e1)
-            best = t if best is None else min(best, t)
-    ck.check(ctx)
-    out["solve_fp32"] = {"ms_per_solve": best, "solves_per_s": 1e3 / best,
-                         "true_residual_sampled": true_residual(X, A_np, pts_np, cfg, rows)}
+    plan_w = ck.Plan(n=n, d=d, dim=dim, block_rows=cfg["block_rows"], prec=ck.FP32_WHT, seed=0, refine_steps=1)
+    out["sketch_fp32_wht"]["rel_err_sampled"] = sampled_sketch_error(ck, Y_of(ck, ctx, plan_w, dense, K, Y), pts_np,
+                                                                      cfg, 0, rows)
+    # the whole solve in the workload's FP32 form: the SIMT contraction and the fast transform
+    for name, pl in [("fp32", plan), ("fp32_wht", plan_w)]:
+        best = None
+        for r in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ck.sketch(ctx, pl, dense, K=K, Y=Y)
+            f = ck.tsqr(ctx, pl, dense, Y)
+            ck.solve(ctx, f, A, X)
+            f.free()
+            e1.record(stream)
+            e1.synchronize()
+            if r:
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+        ck.check(ctx)
+        out["solve_" + name] = {"ms_per_solve": best, "solves_per_s": 1e3 / best,
+                                "true_residual_sampled": true_residual(X, A_np, pts_np, cfg, rows)}
     del K
     torch.cuda.empty_cache()
     out["peak_hbm_GBps"] = hbm

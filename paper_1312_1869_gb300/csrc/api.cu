@@ -247,6 +247,8 @@ Error do_sketch(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_kernel 
   }
   CK_TRY(omega_draw(ctx, plan->n, plan->d, plan->seed, st));
   if (kern->kind == CKINV_DENSE) {
+    if (plan->prec == CKINV_FP32_WHT && sketch_wht_supported(plan->n, plan->d))
+      return sketch_wht_dense(ctx, plan->n, plan->d, kp, K, ldk, Y, ldy, st, row0, m);
     // K is symmetric: its column i is read as row i (16-byte rows for the tensor-core path)
     if (plan->prec != CKINV_FP32 && plan->prec != CKINV_FP32_WHT && ldk % 4 == 0 &&
         (reinterpret_cast<uintptr_t>(K) & 15) == 0)

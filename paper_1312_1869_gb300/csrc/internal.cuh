@@ -212,6 +212,10 @@ Error kernel_matrix(ckinv_ctx *ctx, int64_t n, int dim, const KernelParams &kp, 
 bool sketch_wht_supported(int64_t n, int d);
 Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &kp, const float *points, bool deriv,
                  float *Y, int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
+// The same transform over a materialised K0 (n x n, column-major, ld ldk; symmetric, so row i
+// is read as column i).
+Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp, const float *K, int64_t ldk, float *Y,
+                       int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
                 int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);

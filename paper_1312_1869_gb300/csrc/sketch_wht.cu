@@ -149,6 +149,24 @@ __device__ __forceinline__ void eval_rows(const float *P, int dim, const float (
   }
 }
 
+// A materialised K0: the entries of NR rows against the 32 points k_b = lane + 32 t of the
+// chunk, read from HBM (row i of the symmetric K0 is its column i, contiguous, so a warp's
+// loads are 128-byte lines; streamed, each entry is read once), Rademacher signs applied;
+// with TAIL, entries at or past n are zero.
+template <bool TAIL, int NR>
+__device__ __forceinline__ void load_rows(const float *const (&kc)[NR], int64_t k0, uint32_t smask, int lane, int rem,
+                                          float (&v)[NR][32]) {
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const int kb = lane + 32 * t;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float e = (!TAIL || kb < rem) ? __ldcs(kc[r] + k0 + kb) : 0.f;
+      v[r][t] = flip_if(e, smask, t);
+    }
+  }
+}
+
 // rows (0, 1, ..., R-1) -> (S, S+1, ..., S-1) of the accumulators and coordinates
 template <int R, int S>
 __device__ __forceinline__ void rotate_rows(float (&acc)[R][kWMaxU], float (&xr)[R][3]) {
@@ -175,10 +193,13 @@ __device__ __forceinline__ void rotate_rows(float (&acc)[R][kWMaxU], float (&xr)
 template <bool DERIV, int KIND, int WARPS, int RPW, int NR, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     k_sketch_wht(int64_t n, int64_t row0, int64_t m, int dim, int d, int nchunks, KernelParams kp,
-                 const float *__restrict__ ps, const uint32_t *__restrict__ tsg, const uint32_t *__restrict__ gsw,
+                 const float *__restrict__ ps, const float *__restrict__ Kd, int64_t ldk,
+                 const uint32_t *__restrict__ tsg, const uint32_t *__restrict__ gsw,
                  const uint32_t *__restrict__ gtab, const int *__restrict__ jtab, float *__restrict__ Y, int64_t ldy) {
   constexpr int kThreads = WARPS * 32, kRows = WARPS * RPW;
+  constexpr bool kDense = KIND == CKINV_DENSE;   // entries read from a materialised K0
   static_assert(kRows <= 32 && RPW % NR == 0, "rows per CTA");
+  static_assert(!kDense || RPW == NR, "a materialised K0 takes one group of rows per warp");
   extern __shared__ __align__(16) unsigned char wht_smem[];
   using Smem = WhtSmem<WARPS, NR, kRows>;
   auto &S = *reinterpret_cast<Smem *>(wht_smem);
@@ -189,8 +210,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 
   // chunk ka's points and sign words into buffer b (asynchronous copies, one group)
   auto stage = [&](int ka, int b) {
-    const float *src = ps + (int64_t)ka * chunk_floats;
-    for (int e = threadIdx.x * 4; e < chunk_floats; e += kThreads * 4) cp_async16(&S.sp[b][e], src + e);
+    if constexpr (!kDense) {
+      const float *src = ps + (int64_t)ka * chunk_floats;
+      for (int e = threadIdx.x * 4; e < chunk_floats; e += kThreads * 4) cp_async16(&S.sp[b][e], src + e);
+    }
     if (threadIdx.x < 8)
       cp_async16(&S.ssg[b][4 * threadIdx.x], tsg + (int64_t)ka * 32 + 4 * threadIdx.x);
     else if (threadIdx.x < 16)
@@ -206,11 +229,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   const int64_t rcta = (int64_t)blockIdx.x * kRows;
   const int64_t rbase = rcta + warp * RPW;
   float xr[RPW][3];
+  const float *kc[NR];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int64_t i = min(rbase + r, m - 1);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) xr[r][c] = c < dim ? ps[(row0 + i) * dim + c] : 0.f;
+    for (int c = 0; c < 3; ++c) xr[r][c] = (!kDense && c < dim) ? ps[(row0 + i) * dim + c] : 0.f;
+    if (r < NR) kc[r] = kDense ? Kd + (row0 + i) * ldk : nullptr;
   }
   float acc[RPW][kWMaxU];
 #pragma unroll
@@ -240,10 +265,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     for (int g = 0; g < RPW / NR; ++g) {
       float v[NR][32];
       const float(&xw)[NR][3] = *reinterpret_cast<const float(*)[NR][3]>(&xr[0][0]);
-      if (pad_far(KIND, DERIV) || rem == kWB)
+      if constexpr (kDense) {
+        if (rem == kWB)
+          load_rows<false, NR>(kc, k0, smask, lane, rem, v);
+        else
+          load_rows<true, NR>(kc, k0, smask, lane, rem, v);
+      } else if (pad_far(KIND, DERIV) || rem == kWB) {
         eval_rows<DERIV, KIND, false, NR>(P, dim, xw, inv_l, smask, lane, rem, v);
-      else
+      } else {
         eval_rows<DERIV, KIND, !pad_far(KIND, DERIV), NR>(P, dim, xw, inv_l, smask, lane, rem, v);
+      }
       wht1024_rows<NR>(v, wb, lane);
       __syncwarp();
 #pragma unroll
@@ -369,15 +400,16 @@ constexpr int kCfgWarps = 4, kCfgRowsPerWarp = 2, kCfgPair = 2, kCfgMinBlocks = 
 
 template <bool DERIV, int KIND>
 Error launch_wht(int64_t n, int64_t row0, int64_t m, int dim, int d, int nchunks, const KernelParams &kp,
-                 const float *ps, const uint32_t *tsg, const uint32_t *gsw, const uint32_t *gtab, const int *jtab,
-                 float *Y, int64_t ldy, cudaStream_t st) {
+                 const float *ps, const float *Kd, int64_t ldk, const uint32_t *tsg, const uint32_t *gsw,
+                 const uint32_t *gtab, const int *jtab, float *Y, int64_t ldy, cudaStream_t st) {
   auto kfn = k_sketch_wht<DERIV, KIND, kCfgWarps, kCfgRowsPerWarp, kCfgPair, kCfgMinBlocks>;
   constexpr size_t smem = sizeof(WhtSmem<kCfgWarps, kCfgPair, kCfgWarps * kCfgRowsPerWarp>);
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const dim3 grid((unsigned)ceil_div(m, kCfgWarps * kCfgRowsPerWarp));
   note_launch();
-  kfn<<<grid, kCfgWarps * 32, smem, st>>>(n, row0, m, dim, d, nchunks, kp, ps, tsg, gsw, gtab, jtab, Y, ldy);
+  kfn<<<grid, kCfgWarps * 32, smem, st>>>(n, row0, m, dim, d, nchunks, kp, ps, Kd, ldk, tsg, gsw, gtab, jtab, Y,
+                                          ldy);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
@@ -419,13 +451,43 @@ Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &
   if (cudaGetLastError() != cudaSuccess) e = fail(CKINV_ECUDA, "structured sketch: set-up launch failed");
   if (e.st == CKINV_OK) {
     if (kp.kind == CKINV_SE)
-      e = deriv ? launch_wht<true, CKINV_SE>(n, row0, m, dim, d, nchunks, kp, ps, tsg, gsw, gtab, jtab, Y, ldy, st)
-                : launch_wht<false, CKINV_SE>(n, row0, m, dim, d, nchunks, kp, ps, tsg, gsw, gtab, jtab, Y, ldy, st);
+      e = deriv ? launch_wht<true, CKINV_SE>(n, row0, m, dim, d, nchunks, kp, ps, nullptr, 0, tsg, gsw, gtab, jtab, Y,
+                                             ldy, st)
+                : launch_wht<false, CKINV_SE>(n, row0, m, dim, d, nchunks, kp, ps, nullptr, 0, tsg, gsw, gtab, jtab, Y,
+                                              ldy, st);
     else
-      e = deriv ? launch_wht<true, CKINV_MATERN52>(n, row0, m, dim, d, nchunks, kp, ps, tsg, gsw, gtab, jtab, Y, ldy, st)
-                : launch_wht<false, CKINV_MATERN52>(n, row0, m, dim, d, nchunks, kp, ps, tsg, gsw, gtab, jtab, Y, ldy,
-                                                    st);
+      e = deriv ? launch_wht<true, CKINV_MATERN52>(n, row0, m, dim, d, nchunks, kp, ps, nullptr, 0, tsg, gsw, gtab,
+                                                   jtab, Y, ldy, st)
+                : launch_wht<false, CKINV_MATERN52>(n, row0, m, dim, d, nchunks, kp, ps, nullptr, 0, tsg, gsw, gtab,
+                                                    jtab, Y, ldy, st);
   }
+  cudaFreeAsync(scratch, st);
+  return e;
+}
+
+Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp, const float *K, int64_t ldk, float *Y,
+                       int64_t ldy, cudaStream_t st, int64_t row0, int64_t m) {
+  if (m < 0) m = n;
+  if (!sketch_wht_supported(n, d)) return fail(CKINV_EUNSUPPORTED, "structured sketch: needs N >= 1024, d <= 512");
+  if (m == 0) return ok();
+  const int nchunks = (int)ceil_div(n, kWB);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t tab_bytes = up(sizeof(uint32_t) * 32 * kWMaxU);
+  const size_t mask_bytes = up(sizeof(uint32_t) * 32 * (size_t)nchunks);
+  unsigned char *scratch = nullptr;
+  CK_CUDA(dev_alloc(&scratch, 2 * tab_bytes + 2 * mask_bytes, st));
+  uint32_t *gtab = reinterpret_cast<uint32_t *>(scratch);
+  int *jtab = reinterpret_cast<int *>(scratch + tab_bytes);
+  uint32_t *tsg = reinterpret_cast<uint32_t *>(scratch + 2 * tab_bytes);
+  uint32_t *gsw = reinterpret_cast<uint32_t *>(scratch + 2 * tab_bytes + mask_bytes);
+  note_launch();
+  k_wht_slots<<<1, 256, 0, st>>>(ctx->om.cols, d, gtab, jtab);
+  note_launch();
+  k_wht_masks<<<(unsigned)ceil_div((int64_t)nchunks * 32, 256), 256, 0, st>>>(ctx->om.bits, n, nchunks, gtab, tsg, gsw);
+  Error e = ok();
+  if (cudaGetLastError() != cudaSuccess) e = fail(CKINV_ECUDA, "structured sketch: set-up launch failed");
+  if (e.st == CKINV_OK)
+    e = launch_wht<false, CKINV_DENSE>(n, row0, m, 1, d, nchunks, kp, nullptr, K, ldk, tsg, gsw, gtab, jtab, Y, ldy, st);
   cudaFreeAsync(scratch, st);
   return e;
 }

@@ -93,10 +93,12 @@ def test_derivative_sketch_matches_oracle(ctx, prec, tol, kind):
     assert rel(host(Yd), Yo) <= tol
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16x2", 3e-5), ("bf16", 4e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16x2", 3e-5), ("bf16", 4e-3),
+                                      ("fp32_wht", 1e-5)])
 @pytest.mark.parametrize("n,d", [(1536, 64), (1000, 272)])
 def test_dense_sketch_matches_oracle(ctx, prec, tol, n, d):
-    """Materialised K (the plain-method workload with K in HBM): SIMT FP32 or tensor cores."""
+    """Materialised K (the plain-method workload with K in HBM): SIMT FP32, tensor cores, or
+    the fast transform over K's columns."""
     pts = synth.points(n, 3, 2).astype(np.float64)
     K = okk.kernel_matrix(pts, pts, okk.MATERN52, 0.15, 1.0)
     plan = ck.Plan(n=n, d=d, dim=3, seed=0, prec=ck.PRECISIONS[prec])
