@@ -421,8 +421,8 @@ def run_projection(ck, ctx, dev, n_new=4096):
 def run_blocking_simulation(ck, ctx, dev, sizes=(1000, 5000, 10000, 50000), d=512, m=16, tau=1e-3):
     """The paper's blocking simulation (Sec. 5.1): K = E D E^T (E orthonormalised Gaussian,
     eigenvalues exp(-0.01 i)) at n = 1000 .. 50000, solved through the materialised path with
-    each of the four Omega choices (Walsh-Hadamard, scaled Gaussian, Hartley, cosine), FP32
-    form.  K is built on the GPU from host-drawn factors (input generation, untimed; rank
+    each of the four Omega choices (Walsh-Hadamard - as the fast transform and as a dense
+    contraction - scaled Gaussian, Hartley, cosine), FP32 forms.  K is built on the GPU from host-drawn factors (input generation, untimed; rank
     min(n, 1024): the eigenvalues beyond are below exp(-10.24) = 3.6e-5 of the largest).
     Per size and Omega: the solve (sketch, TSQR, core, refined solve of m right-hand sides)
     timed with CUDA events (best of 2 after an untimed run) and the residual of its X against
@@ -431,7 +431,10 @@ def run_blocking_simulation(ck, ctx, dev, sizes=(1000, 5000, 10000, 50000), d=51
     stream = torch.cuda.current_stream(dev)
     out = {"d": d, "m": m, "nugget": tau, "rank": "min(n, 1024)",
            "timing": "CUDA events, best of 2 after one untimed run"}
-    kinds = [("wht", ck.WHT), ("gaussian", ck.GAUSSIAN), ("hartley", ck.HARTLEY), ("cosine", ck.COSINE)]
+    # the structured Walsh-Hadamard Omega applied as a fast transform (FP32), and as the
+    # compensated dense contraction for comparison; the other three are dense Omega (SIMT GEMM)
+    kinds = [("wht", ck.WHT, ck.FP32_WHT), ("wht_dense_contraction", ck.WHT, ck.FP32), ("gaussian", ck.GAUSSIAN, ck.FP32),
+             ("hartley", ck.HARTLEY, ck.FP32), ("cosine", ck.COSINE, ck.FP32)]
     for n in sizes:
         E, D = synth.ede_factors(n, seed=0, rank=min(n, 1024))
         Et = torch.from_numpy(E.astype(np.float32)).to(dev)
@@ -442,9 +445,9 @@ def run_blocking_simulation(ck, ctx, dev, sizes=(1000, 5000, 10000, 50000), d=51
         rows = np.linspace(0, n - 1, 48).astype(np.int64)
         Krows = K[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
         rec = {}
-        for name, kind in kinds:
+        for name, kind, prec in kinds:
             plan = ck.Plan(n=n, d=min(d, n // 2 // 16 * 16), block_rows=max(1024, 2 * d) if n >= 4 * d else 0,
-                           prec=ck.FP32, seed=0, refine_steps=1, omega_kind=kind)
+                           prec=prec, seed=0, refine_steps=1, omega_kind=kind)
             dense = ck.Kernel(ck.DENSE, 0, 0, tau)
             best, X = None, None
             for r in range(3):
