@@ -6,9 +6,11 @@
 // application of Q to a coefficient block).
 //
 // CTA tile BM x BN, thread tile TM x TN (two TM/2 x TN/2 quadrants, so that the shared
-// memory reads of a warp are conflict-free 16-byte vectors), BK = 8 deep, double-buffered
-// through registers: the next k-slab is fetched from global memory while the current one
-// is multiplied.  Split-K over gridDim.z writes one partial product per split to a
+// memory reads of a warp are conflict-free 16-byte vectors), BK = 8 deep (64 FP32 or 32 FP64
+// rows for the narrow 32 x 32 tile, whose loop would otherwise wait out one global round trip
+// per 8 rows),
+// double-buffered through registers: the next k-slab is fetched from global memory while the
+// current one is multiplied.  Split-K over gridDim.z writes one partial product per split to a
 // workspace, and a second kernel adds them in split order (so results do not depend on
 // the order in which blocks finish).
 #include "internal.cuh"
@@ -16,12 +18,11 @@
 namespace ckinv {
 namespace {
 
-template <typename T, int BM, int BN, int TM, int TN_, bool TRANSA>
+template <typename T, int BM, int BN, int TM, int TN_, bool TRANSA, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN_), (TM * TN_ >= 64) ? 2 : 3)
     k_gemm(int M, int N, int K, T alpha, const T *__restrict__ A, int64_t lda, int64_t sA,
            const T *__restrict__ B, int64_t ldb, int64_t sB, T beta, T *__restrict__ C, int64_t ldc, int64_t sC,
            int ksplit, T *__restrict__ part, int nb1, int64_t sA2, int64_t sB2, int64_t sC2) {
-  constexpr int BK = 8;
   constexpr int NTX = BN / TN_, NTY = BM / TM;
   constexpr int NT = NTX * NTY;
   constexpr int LA = BM * BK / NT;   // A elements loaded per thread per slab
@@ -152,7 +153,7 @@ __global__ void k_splitk_reduce(int M, int N, int batch, int ksplit, const T *pa
   }
 }
 
-template <typename T, int BM, int BN, int TM, int TN_>
+template <typename T, int BM, int BN, int TM, int TN_, int BK = 8>
 void launch_shape(bool transA, int M, int N, int K, T alpha, const T *A, int64_t lda, int64_t sA, const T *B,
                   int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC, int batch, int ksplit,
                   T *part, int nb1, int64_t sA2, int64_t sB2, int64_t sC2, cudaStream_t st) {
@@ -160,11 +161,11 @@ void launch_shape(bool transA, int M, int N, int K, T alpha, const T *A, int64_t
   constexpr int NT = (BM / TM) * (BN / TN_);
   note_launch();
   if (transA)
-    k_gemm<T, BM, BN, TM, TN_, true><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                          sC, ksplit, part, nb1, sA2, sB2, sC2);
+    k_gemm<T, BM, BN, TM, TN_, true, BK><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                              sC, ksplit, part, nb1, sA2, sB2, sC2);
   else
-    k_gemm<T, BM, BN, TM, TN_, false><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                           sC, ksplit, part, nb1, sA2, sB2, sC2);
+    k_gemm<T, BM, BN, TM, TN_, false, BK><<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                               sC, ksplit, part, nb1, sA2, sB2, sC2);
 }
 
 }  // namespace
@@ -174,12 +175,17 @@ Error gemm_simt(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha,
                 const T *B, int64_t ldb, int64_t sB, T beta, T *C, int64_t ldc, int64_t sC, int nb1, int64_t sA2,
                 int64_t sB2, int64_t sC2, int nb2, cudaStream_t st) {
   const int batch = nb1 * nb2;
-  // tile choice: 128 x 128 (8 x 8 per thread) for large FP32 outputs, else 64 x 64 (4 x 4)
+  // tile choice: 128 x 128 (8 x 8 per thread) for large FP32 outputs, 32 x 32 (2 x 2) for
+  // outputs of at most 32 x 32 (the inner products of narrow Householder blocks, where a
+  // 64 x 64 tile would compute 4 to 16 times the output), else 64 x 64 (4 x 4)
   const bool big = (sizeof(T) == 4) && M >= 256 && N >= 128;
-  const int bm = big ? 128 : 64, bn = big ? 128 : 64;
+  const bool small = M <= 32 && N <= 32;
+  const int bm = big ? 128 : small ? 32 : 64, bn = bm;
   const int64_t tiles = ceil_div(M, bm) * ceil_div(N, bn) * (int64_t)batch;
   int ksplit = 1;
-  const int64_t target = 2LL * ctx->sm_count;
+  // split K while the output tiles alone would leave SMs idle: up to four CTAs per SM for FP32
+  // (these products are short of parallelism, not of arithmetic), two for FP64
+  const int64_t target = (sizeof(T) == 4 ? 4LL : 2LL) * ctx->sm_count;
   if (tiles < target && K >= 256) {
     ksplit = (int)std::min<int64_t>(std::max<int64_t>(1, target / tiles), K / 128);
     ksplit = std::max(ksplit, 1);
@@ -189,6 +195,9 @@ Error gemm_simt(const ckinv_ctx *ctx, bool transA, int M, int N, int K, T alpha,
   if (big)
     launch_shape<T, 128, 128, 8, 8>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
                                     part, nb1, sA2, sB2, sC2, st);
+  else if (small)   // deep k-slabs (36 KB of static shared memory): a narrow tile's loop is bound by round trips
+    launch_shape<T, 32, 32, 2, 2, sizeof(T) == 4 ? 64 : 32>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                                            ldc, sC, batch, ksplit, part, nb1, sA2, sB2, sC2, st);
   else
     launch_shape<T, 64, 64, 4, 4>(transA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, ksplit,
                                   part, nb1, sA2, sB2, sC2, st);
