@@ -94,23 +94,42 @@ __device__ __forceinline__ dfloat operator+(dprod x, dfloat c) { return fma_dd(x
 __device__ __forceinline__ dfloat operator-(dfloat c, dprod x) { return fma_dd(-x.a, x.b, c); }
 __device__ __forceinline__ dfloat operator-(dprod x, dfloat c) { return fma_dd(x.a, x.b, -c); }
 
+// The hardware's approximate reciprocal and square root (relative error about 2^-22): the
+// corrections below square the precision, so the IEEE-rounded FP32 sequences (longer, and
+// branching for special operands) are not needed.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
-  // long division: q1 from the leading halves, then the remainder's quotient as correction
-  const float q1 = a.hi / b.hi;
+  // long division by an approximate reciprocal: each remainder's quotient is a correction
+  // about 2^-22 smaller than the previous one, three terms give the full precision
+  const float rb = rcp_approx(b.hi);
+  const float q1 = a.hi * rb;
   const dfloat r = a - mul(b, dfloat(q1, 0.f));
-  const float q2 = r.hi / b.hi;
+  const float q2 = r.hi * rb;
   const dfloat r2 = r - mul(b, dfloat(q2, 0.f));
-  const float q3 = r2.hi / b.hi;
+  const float q3 = r2.hi * rb;
   const dfloat q = fast_two_sum(q1, q2);
   return q + dfloat(q3, 0.f);
 }
 
 __device__ __forceinline__ dfloat sqrt(dfloat a) {
   if (!(a.hi > 0.f)) return dfloat(0.f, 0.f);
-  // one Newton correction of the FP32 root: s + (a - s^2) / (2 s)
-  const float s = sqrtf(a.hi);
-  const dfloat r = a - mul(dfloat(s, 0.f), dfloat(s, 0.f));
-  return fast_two_sum(s, r.hi / (2.f * s));
+  // two corrections of the approximate root: s + (a - s^2) / (2 s), twice
+  float s = sqrt_approx(a.hi);
+  dfloat r = a - mul(dfloat(s, 0.f), dfloat(s, 0.f));
+  const float h = 0.5f * rcp_approx(s);
+  const dfloat s1 = fast_two_sum(s, r.hi * h);
+  r = a - mul(s1, s1);
+  return s1 + dfloat(r.hi * h, 0.f);
 }
 
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
