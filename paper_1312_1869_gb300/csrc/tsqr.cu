@@ -790,6 +790,36 @@ Error apply_q(const ckinv_ctx *ctx, const Stage<T> &s, int d, const double *Xslo
   return ok();
 }
 
+// Leaves of one height whose Q_hat rows follow each other at a fixed stride in one output.
+struct LeafRun {
+  int first, count, h;
+  float *dst;          // Q_hat rows of leaf `first`
+  int64_t ldq, stride; // leading dimension, rows between consecutive leaves
+};
+
+// The leaf stage of the top-down pass for FP32 leaves, written straight into Q_hat: leaf p's
+// rows are Q_p [X_p; 0] = [X_p; 0] - V_p (T_p (V_p[0:d]^T X_p)); the product goes to Q_hat's
+// rows as -V Z2, and X is then added to each leaf's first d rows (the sum the GEMM's epilogue
+// would form, in the same FP32 operation), so no staging array is filled with [X; 0] and none
+// is copied out.
+Error apply_q_leaves(const ckinv_ctx *ctx, const Stage<float> &s, int d, const double *Xslot, float *X0, float *Z1,
+                     float *Z2, const std::vector<LeafRun> &runs, cudaStream_t st) {
+  const int H = s.H, P = s.P;
+  const int64_t sM = (int64_t)H * d, sD = (int64_t)d * d;
+  dim3 g((unsigned)std::min(d, 128), P);
+  note_launch();
+  k_init_qs<float><<<g, 256, 0, st>>>(Xslot, s.top, d, d, X0);   // each leaf's X, d x d
+  CK_CUDA(cudaGetLastError());
+  CK_TRY(gemm_batched<float>(ctx, true, d, d, d, 1.f, s.Vx, H, sM, X0, d, sD, 0.f, Z1, d, sD, P, st));
+  CK_TRY(gemm_batched<float>(ctx, false, d, d, d, 1.f, s.Tm, d, sD, Z1, d, sD, 0.f, Z2, d, sD, P, st));
+  for (const LeafRun &r : runs) {
+    CK_TRY(gemm_batched<float>(ctx, false, r.h, d, d, -1.f, s.Vx + r.first * sM, H, sM, Z2 + r.first * sD, d, sD,
+                               0.f, r.dst, r.ldq, r.stride, r.count, st));
+    CK_TRY(axpby<float>(d, d, 1.f, X0 + r.first * sD, d, sD, 1.f, r.dst, r.ldq, r.stride, r.count, st));
+  }
+  return ok();
+}
+
 struct Level {
   std::vector<int> top, bot;   // combines (top slot, bottom slot)
   bool fp64 = false;
@@ -1128,11 +1158,27 @@ Error tsqr_impl(ckinv_ctx *ctx, const std::vector<TsqrProblem> &probs, int d, in
       }
     }
     if (e.st) break;
-    if ((e = apply_q<TL>(ctx, leaf, d, Xslot, (TL *)Qs, (TL *)Z1, (TL *)Z2, st)).st) break;
-    {
+    if constexpr (LEAF64) {
+      if ((e = apply_q<TL>(ctx, leaf, d, Xslot, (TL *)Qs, (TL *)Z1, (TL *)Z2, st)).st) break;
       dim3 g((unsigned)std::min(d, 128), L);
       note_launch();
       k_leaf_q<TL><<<g, 256, 0, st>>>((TL *)Qs, Hl, d, d_dst, d_ldq, d_rows);
+    } else {
+      // runs of equal-height leaves of one problem, consecutive in its Q_hat
+      std::vector<LeafRun> runs;
+      for (int i = 0; i < L; ++i) {
+        if (!runs.empty()) {
+          LeafRun &r = runs.back();
+          const int last = r.first + r.count - 1;
+          if (rows[i] == r.h && lldq[i] == r.ldq && ldst[i] == ldst[last] + r.h && (r.count == 1 || r.stride == r.h)) {
+            r.stride = r.h;
+            ++r.count;
+            continue;
+          }
+        }
+        runs.push_back(LeafRun{i, 1, rows[i], ldst[i], lldq[i], rows[i]});
+      }
+      if ((e = apply_q_leaves(ctx, leaf, d, Xslot, (float *)Qs, (float *)Z1, (float *)Z2, runs, st)).st) break;
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
