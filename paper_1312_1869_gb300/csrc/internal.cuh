@@ -215,7 +215,12 @@ Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &
 // The same transform over a materialised K0 (n x n, column-major, ld ldk; symmetric, so row i
 // is read as column i).
 Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp, const float *K, int64_t ldk, float *Y,
-                       int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);
+                       int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1,
+                       const uint32_t *bits = nullptr, const int32_t *cols = nullptr);
+// B (d x d, FP64, ld d) = scale Omega^T X for X n x d (FP32, ld ldx), with Omega's signs and
+// columns given: the fast transform over X's d columns in FP32, transposed and widened.
+Error omega_t_times_wht(ckinv_ctx *ctx, int64_t n, int d, const float *X, int64_t ldx, const uint32_t *bits,
+                        const int32_t *cols, double scale, double *B, cudaStream_t st);
 Error sketch_tc(ckinv_ctx *ctx, int64_t n, int dim, int d, int nsplit,
                 const KernelParams &kp, const float *points, bool deriv, float *Y,
                 int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1);

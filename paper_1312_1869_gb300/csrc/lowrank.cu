@@ -847,6 +847,8 @@ Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
     CK_TRY(tsprod(ctx, f->n, d, d, f->omega_dense, f->n, nullptr, nullptr, 0.0, f->Q, f->n, f->B, st));
   else if (f->n % 4 == 0 && f->prec == CKINV_BF16)
     CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
+  else if (f->prec == CKINV_FP32_WHT && sketch_wht_supported(f->n, d))   // the fast transform, FP32
+    CK_TRY(omega_t_times_wht(ctx, f->n, d, f->Q, f->n, f->bits, f->cols, f->omega_scale, f->B, st));
   else
     CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
   return core_from_b(ctx, f, st);

@@ -466,8 +466,11 @@ Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &
 }
 
 Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp, const float *K, int64_t ldk, float *Y,
-                       int64_t ldy, cudaStream_t st, int64_t row0, int64_t m) {
+                       int64_t ldy, cudaStream_t st, int64_t row0, int64_t m, const uint32_t *bits,
+                       const int32_t *cols) {
   if (m < 0) m = n;
+  if (!bits) bits = ctx->om.bits;
+  if (!cols) cols = ctx->om.cols;
   if (!sketch_wht_supported(n, d)) return fail(CKINV_EUNSUPPORTED, "structured sketch: needs N >= 1024, d <= 512");
   if (m == 0) return ok();
   const int nchunks = (int)ceil_div(n, kWB);
@@ -481,14 +484,41 @@ Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp,
   uint32_t *tsg = reinterpret_cast<uint32_t *>(scratch + 2 * tab_bytes);
   uint32_t *gsw = reinterpret_cast<uint32_t *>(scratch + 2 * tab_bytes + mask_bytes);
   note_launch();
-  k_wht_slots<<<1, 256, 0, st>>>(ctx->om.cols, d, gtab, jtab);
+  k_wht_slots<<<1, 256, 0, st>>>(cols, d, gtab, jtab);
   note_launch();
-  k_wht_masks<<<(unsigned)ceil_div((int64_t)nchunks * 32, 256), 256, 0, st>>>(ctx->om.bits, n, nchunks, gtab, tsg, gsw);
+  k_wht_masks<<<(unsigned)ceil_div((int64_t)nchunks * 32, 256), 256, 0, st>>>(bits, n, nchunks, gtab, tsg, gsw);
   Error e = ok();
   if (cudaGetLastError() != cudaSuccess) e = fail(CKINV_ECUDA, "structured sketch: set-up launch failed");
   if (e.st == CKINV_OK)
     e = launch_wht<false, CKINV_DENSE>(n, row0, m, 1, d, nchunks, kp, nullptr, K, ldk, tsg, gsw, gtab, jtab, Y, ldy, st);
   cudaFreeAsync(scratch, st);
+  return e;
+}
+
+namespace {
+// B[j + i d] = (double) Bt[i + j d]
+__global__ void k_transpose_widen(int d, const float *__restrict__ Bt, double *__restrict__ B) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += gridDim.x * blockDim.x) {
+    const int i = e % d, j = e / d;
+    B[j + (int64_t)i * d] = (double)Bt[e];
+  }
+}
+}  // namespace
+
+Error omega_t_times_wht(ckinv_ctx *ctx, int64_t n, int d, const float *X, int64_t ldx, const uint32_t *bits,
+                        const int32_t *cols, double scale, double *B, cudaStream_t st) {
+  float *Bt = nullptr;
+  CK_CUDA(dev_alloc(&Bt, sizeof(float) * (size_t)d * d, st));
+  KernelParams kp{};
+  kp.kind = CKINV_DENSE;
+  kp.scale = scale;
+  Error e = sketch_wht_dense(ctx, n, d, kp, X, ldx, Bt, d, st, 0, d, bits, cols);
+  if (e.st == CKINV_OK) {
+    note_launch();
+    k_transpose_widen<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d * d, 256), 1024), 256, 0, st>>>(d, Bt, B);
+    if (cudaGetLastError() != cudaSuccess) e = fail(CKINV_ECUDA, "transpose launch failed");
+  }
+  cudaFreeAsync(Bt, st);
   return e;
 }
 

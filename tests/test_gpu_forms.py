@@ -34,7 +34,7 @@ from gpu_util import col, host, rel
 pytestmark = pytest.mark.gpu
 
 ck = None
-FORMS = [("bf16", 1), ("bf16x2", 2), ("bf16x3", 3)]
+FORMS = [("bf16", 1), ("bf16x2", 2), ("bf16x3", 3), ("fp32_wht", 3)]   # FP32 entries carry 24 bits, as 3 terms do
 BAR = 1e-4
 
 
