@@ -553,13 +553,13 @@ Error nll_grad_enqueue(ckinv_ctx *ctx, const ckinv_plan_desc *plan, const ckinv_
     if ((e = tsprod(ctx, n, d, 1, f->Q, n, nullptr, nullptr, 0, alpha, n, beta, st)).st) break;
     if ((e = tsprod(ctx, n, d, 1, Yd, n, nullptr, nullptr, 0, alpha, n, g3, st)).st) break;
     if ((e = tsprod(ctx, n, d, d, f->Q, n, nullptr, nullptr, 0, Yd, n, G1, st)).st) break;
-    if (n % 4 == 0 && plan->prec == CKINV_BF16) {
+    if (omega_by_transform(plan->prec, n, d)) {
+      // G2 = Omega^T Yd through the fast transform over Yd's columns (FP32)
+      if ((e = omega_t_times_wht(ctx, n, d, Yd, n, f->bits, f->cols, f->omega_scale, G2, st)).st) break;
+    } else if (n % 4 == 0 && plan->prec == CKINV_BF16) {
       // G2 = Omega^T Yd on the tensor cores (rows of A are the columns of Yd)
       if ((e = omega_draw(ctx, n, d, plan->seed, st)).st) break;
       if ((e = dense_tc(ctx, d, n, d, 3, Yd, n, f->omega_scale, nullptr, 0, G2, d, 1, st)).st) break;
-    } else if (plan->prec == CKINV_FP32_WHT && sketch_wht_supported(n, d)) {
-      // G2 = Omega^T Yd through the fast transform over Yd's columns (FP32)
-      if ((e = omega_t_times_wht(ctx, n, d, Yd, n, f->bits, f->cols, f->omega_scale, G2, st)).st) break;
     } else if ((e = tsprod(ctx, n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, Yd, n, G2, st)).st) {
       break;
     }

@@ -217,6 +217,11 @@ Error sketch_wht(ckinv_ctx *ctx, int64_t n, int dim, int d, const KernelParams &
 Error sketch_wht_dense(ckinv_ctx *ctx, int64_t n, int d, const KernelParams &kp, const float *K, int64_t ldk, float *Y,
                        int64_t ldy, cudaStream_t st, int64_t row0 = 0, int64_t m = -1,
                        const uint32_t *bits = nullptr, const int32_t *cols = nullptr);
+// Whether a form applies the Walsh-Hadamard Omega to an n x d matrix (Omega^T X) by the fast
+// transform: the BF16 and fast-transform forms, where N >= 1024.
+inline bool omega_by_transform(int prec, int64_t n, int d) {
+  return (prec == CKINV_BF16 || prec == CKINV_FP32_WHT) && sketch_wht_supported(n, d);
+}
 // B (d x d, FP64, ld d) = scale Omega^T X for X n x d (FP32, ld ldx), with Omega's signs and
 // columns given: the fast transform over X's d columns in FP32, transposed and widened.
 Error omega_t_times_wht(ckinv_ctx *ctx, int64_t n, int d, const float *X, int64_t ldx, const uint32_t *bits,

@@ -841,14 +841,17 @@ Error gemm_small_dev(int d, int m, const double *A, const double *Bm, double *C,
 Error lowrank_core(ckinv_ctx *ctx, ckinv_factor *f, cudaStream_t st) {
   const int d = f->d;
   // B = Omega^T Q_hat  (B^T = Q_hat^T Omega: rows of A are the columns of Q_hat).  The BF16
-  // form uses the tensor cores with Q_hat split into three BF16 terms (~1e-5 relative); the
-  // other forms keep the FP32-accurate contraction (FP64 across 256-row chunks)
+  // and fast-transform forms apply the Walsh-Hadamard Omega as the fast transform over
+  // Q_hat's d columns in FP32 (~6e-7 relative; for the BF16 form that replaces a three-term
+  // tensor-core product at ~1e-5).  The FP32-level reference forms keep the compensated
+  // contraction with Omega from its bits (FP64 across 256-row chunks): their FP64-leaf
+  // likelihood is pinned tighter than FP32 sums of B allow.  A dense Omega: FP32 contraction.
   if (f->omega_dense)        // a dense Omega (Gaussian, Hartley, cosine): B = Omega^T Q_hat in FP32
     CK_TRY(tsprod(ctx, f->n, d, d, f->omega_dense, f->n, nullptr, nullptr, 0.0, f->Q, f->n, f->B, st));
+  else if (omega_by_transform(f->prec, f->n, d))
+    CK_TRY(omega_t_times_wht(ctx, f->n, d, f->Q, f->n, f->bits, f->cols, f->omega_scale, f->B, st));
   else if (f->n % 4 == 0 && f->prec == CKINV_BF16)
     CK_TRY(dense_tc(ctx, d, f->n, d, 3, f->Q, f->n, f->omega_scale, nullptr, 0, f->B, d, 1, st));
-  else if (f->prec == CKINV_FP32_WHT && sketch_wht_supported(f->n, d))   // the fast transform, FP32
-    CK_TRY(omega_t_times_wht(ctx, f->n, d, f->Q, f->n, f->bits, f->cols, f->omega_scale, f->B, st));
   else
     CK_TRY(tsprod(ctx, f->n, d, d, nullptr, 0, f->bits, f->cols, f->omega_scale, f->Q, f->n, f->B, st));
   return core_from_b(ctx, f, st);

@@ -208,9 +208,9 @@ def test_tsqr_bf16_forms_tensor_core_gemms(ctx, n, d, b, f64):
                                         (3000, 128, 1024, "fp32_wht")])
 def test_core_matches_oracle(ctx, n, d, b, prec):
     """B = Omega^T Q_hat, C' = R^T + tau B and log det K_tilde from the FP64 LUs (32-column
-    panels: 16 of them at d = 512).  The BF16 form takes B on the tensor cores (Q_hat in three
-    BF16 terms) and its TSQR's GEMMs there too (~1e-5); the fast-transform form applies Omega
-    to Q_hat's columns by the transform in FP32 (n = 3000: a zero-padded last chunk)."""
+    panels: 16 of them at d = 512).  The BF16 and fast-transform forms apply the
+    Walsh-Hadamard Omega to Q_hat's columns by the fast transform in FP32 (n = 3000: a
+    zero-padded last chunk); the BF16 form runs its TSQR's GEMMs on the tensor cores (~1e-5)."""
     tau = 1e-3
     rng = np.random.default_rng(5)
     Y = rng.standard_normal((n, d)).astype(np.float32)
