@@ -79,6 +79,35 @@ def test_sketch_matches_oracle(ctx, prec, tol, n, d, kind, ell, dim):
     assert err <= tol
 
 
+@pytest.mark.parametrize("n,d,dim,kind,deriv", [
+    (1025, 64, 1, okk.SE, False),         # one live entry in the second chunk
+    (1024, 16, 2, okk.MATERN52, False),   # exactly one chunk; one output slot a lane
+    (4100, 512, 3, okk.SE, False),        # sixteen slots a lane, a 4-entry last chunk
+    (3000, 96, 3, okk.MATERN52, True),    # Matern derivative: the masked last chunk
+    (2049, 48, 2, okk.SE, True),          # SE derivative: clamped distances to the padding
+])
+def test_fast_transform_sketch_edges(ctx, n, d, dim, kind, deriv):
+    """The FP32 fast-transform sketch at the shapes its chunking and output slots make
+    special, against the oracle's sketch (bar 1e-5, the FP32 Y bar), and a row range ending
+    in a partial 8-row block bit-identical to the same rows of the whole sketch."""
+    pts = synth.points(n, dim, 7)
+    plan = ck.Plan(n=n, d=d, dim=dim, prec=ck.FP32_WHT, seed=13)
+    kern = ck.Kernel(kind, 0.2, 0.9, 1e-4)
+    P = torch.from_numpy(pts).cuda()
+    Y = ck.sketch_dlogl(ctx, plan, kern, P) if deriv else ck.sketch(ctx, plan, kern, P)
+    torch.cuda.synchronize()
+    ck.check(ctx)
+    Yo = osk.sketch(pts.astype(np.float64), kind, 0.2, 0.9, oom.omega_matrix(n, d, 13), derivative=deriv)
+    err = rel(host(Y), Yo)
+    print("fast-transform sketch n=%d d=%d dim=%d kind=%d deriv=%d: err %.3e" % (n, d, dim, kind, deriv, err))
+    assert err <= 1e-5
+    if not deriv:
+        r0, m = 5, n - 11                 # m % 8 != 0
+        Yr = ck.sketch_rows(ctx, plan, kern, r0, m, points=P)
+        torch.cuda.synchronize()
+        assert torch.equal(Yr, Y[r0:r0 + m])
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("bf16", 4e-3), ("fp32_wht", 1e-5)])
 @pytest.mark.parametrize("kind", [okk.SE, okk.MATERN52])
 def test_derivative_sketch_matches_oracle(ctx, prec, tol, kind):
