@@ -67,6 +67,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // In-register Walsh-Hadamard transform of 32 values along the register index.
@@ -256,6 +257,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     if (ka + 1 < nchunks) stage(ka + 1, b ^ 1);
     const int64_t k0 = (int64_t)ka * kWB;
     const int rem = n - k0 < kWB ? (int)(n - k0) : kWB;   // live entries of this chunk
+    if constexpr (kDense) {
+      // the next chunk's lines of this warp's columns into L2 while this one is transformed
+      // (lane l takes line l; lines past n are not touched)
+      const int64_t kn = k0 + kWB + 32 * lane;
+      if (kn < n) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) prefetch_l2(kc[r] + kn);
+      }
+    }
     const uint32_t smask = S.ssg[b][lane];              // signs of this lane's 32 entries
     const uint32_t gsg = S.sgs[b][lane];                // (-1)^popcount(k_a & p_a) of its slots
     const float *P = S.sp[b];
