@@ -704,13 +704,15 @@ def run_ours(args, rank, world, local_rank):
 
 def run_profile(args):
     """A bare loop over one part of the step (the fused sketch, the TSQR with its core, or
-    the whole step) on the workload, optionally at a smaller n: the command the ncu captures
-    of profiles/ run."""
+    the whole step) on the workload, or over the sketch of a materialised K (sketch_dense: the
+    65536-point Matern workload, K built untimed), optionally at a smaller n: the command the
+    ncu captures of profiles/ run."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1312_1869_gb300 import ckinv as ck
-    cfg = workload_config(args.workload)
+    dense = args.profile_kernel == "sketch_dense"
+    cfg = workload_config("c2_dense_n65536" if dense else args.workload)
     n = args.n or cfg["n"]
     d, m, dim = cfg["d"], cfg["m"], cfg["dim"]
     ctx = ck.Context(0)
@@ -721,11 +723,19 @@ def run_profile(args):
     A = torch.from_numpy(np.ascontiguousarray(synth.rhs(n, m, 0).T)).cuda().t()
     Y = ck.colmajor(n, d)
     X = ck.colmajor(n, m)
-    ck.sketch(ctx, plan, kern, pts, Y=Y)
+    K = None
+    if dense:
+        K = ck.kernel_matrix(ctx, plan, kern, pts)
+        kern = ck.Kernel(ck.DENSE, 0, 0, cfg["tau"])
+        ck.sketch(ctx, plan, kern, K=K, Y=Y)
+    else:
+        ck.sketch(ctx, plan, kern, pts, Y=Y)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(args.warmup + args.steps):
         if i == args.warmup:
             e0.record()
+        if dense:
+            ck.sketch(ctx, plan, kern, K=K, Y=Y)
         if args.profile_kernel in ("sketch", "step"):
             ck.sketch(ctx, plan, kern, pts, Y=Y)
         if args.profile_kernel in ("tsqr", "step"):
@@ -756,7 +766,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the BF16x2, BF16x3 and FP32 forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the likelihood and batched workloads")
-    ap.add_argument("--profile-kernel", default=None, choices=["sketch", "tsqr", "step"],
+    ap.add_argument("--profile-kernel", default=None, choices=["sketch", "sketch_dense", "tsqr", "step"],
                     help="run only `steps` launches of one part of the step (for ncu captures): no JSON contract line")
     ap.add_argument("--n", type=int, default=None, help="override the workload's n (profiling a smaller case)")
     ap.add_argument("--block-rows", type=int, default=None, help="override the workload's TSQR leaf height")

@@ -31,6 +31,7 @@ namespace ckinv {
 namespace {
 
 constexpr int kWB = 1024;             // transform length (chunk of points)
+constexpr int kPfAhead = 2;           // materialised K0: chunks prefetched into L2 ahead of the one in work
 constexpr int kWMaxU = 16;            // output slots per lane: d <= 512
 constexpr int kWPad = 33;             // padded row of the transpose buffers
 
@@ -46,10 +47,11 @@ constexpr float kSeClamp = 1e4f;
 __host__ __device__ constexpr bool pad_far(int kind, bool) { return kind == CKINV_SE; }
 
 // Shared memory of one CTA.  The transpose buffers double, after the last chunk, as the
-// d x ROWS staging tile of the output (column stride ROWS + 1).
-template <int WARPS, int NB, int ROWS>
+// d x ROWS staging tile of the output (column stride ROWS + 1).  A materialised K0 (PTS
+// false) stages no points.
+template <int WARPS, int NB, int ROWS, bool PTS = true>
 struct WhtSmem {
-  float sp[2][kWB * 3];                  // the chunk's points (pre-scaled), two buffers
+  float sp[2][PTS ? kWB * 3 : 4];        // the chunk's points (pre-scaled), two buffers
   uint32_t ssg[2][32];                   // lane l: bit t = sign bit of entry l + 32 t of the chunk
   uint32_t sgs[2][32];                   // lane l: bit u = gather sign of its slot u for the chunk
   static constexpr int kTPad = ROWS + 1;                 // staging tile: row stride of column j
@@ -202,19 +204,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
   static_assert(kRows <= 32 && RPW % NR == 0, "rows per CTA");
   static_assert(!kDense || RPW == NR, "a materialised K0 takes one group of rows per warp");
   extern __shared__ __align__(16) unsigned char wht_smem[];
-  using Smem = WhtSmem<WARPS, NR, kRows>;
+  using Smem = WhtSmem<WARPS, NR, kRows, !kDense>;
   auto &S = *reinterpret_cast<Smem *>(wht_smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float inv_l = kp.inv_l;
   const int nu = (d + 31) / 32;
   const int chunk_floats = kWB * dim;               // a 16-byte multiple for every dim
 
-  // chunk ka's points and sign words into buffer b (asynchronous copies, one group)
+  // chunk ka's points and sign words into buffer b (asynchronous copies, one group); a
+  // materialised K0 needs no points, and each warp reads its sign words itself
   auto stage = [&](int ka, int b) {
-    if constexpr (!kDense) {
-      const float *src = ps + (int64_t)ka * chunk_floats;
-      for (int e = threadIdx.x * 4; e < chunk_floats; e += kThreads * 4) cp_async16(&S.sp[b][e], src + e);
-    }
+    if constexpr (kDense) return;
+    const float *src = ps + (int64_t)ka * chunk_floats;
+    for (int e = threadIdx.x * 4; e < chunk_floats; e += kThreads * 4) cp_async16(&S.sp[b][e], src + e);
     if (threadIdx.x < 8)
       cp_async16(&S.ssg[b][4 * threadIdx.x], tsg + (int64_t)ka * 32 + 4 * threadIdx.x);
     else if (threadIdx.x < 16)
@@ -252,22 +254,48 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     addr2[h] = (S.gtab[lane + 64 * h] & 0x7ffu) | ((S.gtab[lane + 64 * h + 32] & 0x7ffu) << 16);
 
   float *wb = S.buf + warp * NR * 32 * kWPad;
+  // L2 prefetch of chunk ka's 4 KB of each of this warp's columns, issued kPfAhead chunks
+  // before the chunk is read: lane l takes the 64-byte segments l and l + 32 (one prefetch
+  // fills one 64-byte segment); segments past n are not touched
+  auto prefetch_chunk = [&](int ka) {
+    if constexpr (kDense) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t kn = (int64_t)ka * kWB + 16 * (lane + 32 * h);
+        if (kn < n) {
+#pragma unroll
+          for (int r = 0; r < NR; ++r) prefetch_l2(kc[r] + kn);
+        }
+      }
+    }
+  };
+#pragma unroll 1
+  for (int ka = 1; ka < kPfAhead; ++ka) prefetch_chunk(ka);
+  // a materialised K0's sign words, read by each warp one chunk ahead (no block barrier in
+  // its chunk loop: the warps run decoupled)
+  uint32_t smask_next = 0, gsg_next = 0;
+  if constexpr (kDense) {
+    smask_next = __ldg(tsg + lane);
+    gsg_next = __ldg(gsw + lane);
+  }
   for (int ka = 0; ka < nchunks; ++ka) {
     const int b = ka & 1;
     if (ka + 1 < nchunks) stage(ka + 1, b ^ 1);
     const int64_t k0 = (int64_t)ka * kWB;
     const int rem = n - k0 < kWB ? (int)(n - k0) : kWB;   // live entries of this chunk
+    prefetch_chunk(ka + kPfAhead);
+    uint32_t smask, gsg;   // signs of this lane's 32 entries; (-1)^popcount(k_a & p_a) of its slots
     if constexpr (kDense) {
-      // the next chunk's lines of this warp's columns into L2 while this one is transformed
-      // (lane l takes line l; lines past n are not touched)
-      const int64_t kn = k0 + kWB + 32 * lane;
-      if (kn < n) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) prefetch_l2(kc[r] + kn);
+      smask = smask_next;
+      gsg = gsg_next;
+      if (ka + 1 < nchunks) {
+        smask_next = __ldg(tsg + (int64_t)(ka + 1) * 32 + lane);
+        gsg_next = __ldg(gsw + (int64_t)(ka + 1) * 32 + lane);
       }
+    } else {
+      smask = S.ssg[b][lane];
+      gsg = S.sgs[b][lane];
     }
-    const uint32_t smask = S.ssg[b][lane];              // signs of this lane's 32 entries
-    const uint32_t gsg = S.sgs[b][lane];                // (-1)^popcount(k_a & p_a) of its slots
     const float *P = S.sp[b];
     // the warp's rows, NR at a time: the body is kept rolled (unrolled copies overflow the
     // instruction cache); the rows in work are always the first NR, rotated after each group
@@ -297,9 +325,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
       }
       rotate_rows<RPW, NR>(acc, xr);
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (!kDense) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
   }
+  if constexpr (kDense) __syncthreads();   // the staging tile below overlaps other warps' buffers
   // Y = scale * acc: stage the CTA's rows x d block as T[j][row], then write each column's
   // rows as one contiguous segment
   float *T = S.buf;
@@ -407,19 +438,25 @@ __global__ void k_wht_slots(const int32_t *__restrict__ cols, int d, uint32_t *_
 // 4 rows (252 registers, 8 warps an SM): 65.7 ms against 84 ms; 12 warps of 2 rows in one CTA
 // 73 ms, 6 warps x 2 CTAs 67.6 ms, 3 warps x 4 CTAs 67.0 ms.
 constexpr int kCfgWarps = 4, kCfgRowsPerWarp = 2, kCfgPair = 2, kCfgMinBlocks = 3;
+// A materialised K0: one row a warp (96 registers), 5 CTAs = 20 warps resident per SM to
+// cover the streaming loads (2 rows a warp at 168 registers held 12: 3.3 against 3.0 ms for
+// the 17.2 GB K of 65536 points; 4 CTAs at 124 registers: 3.06 ms; 6 spill).
+constexpr int kDnWarps = 4, kDnRowsPerWarp = 1, kDnMinBlocks = 5;
 
 template <bool DERIV, int KIND>
 Error launch_wht(int64_t n, int64_t row0, int64_t m, int dim, int d, int nchunks, const KernelParams &kp,
                  const float *ps, const float *Kd, int64_t ldk, const uint32_t *tsg, const uint32_t *gsw,
                  const uint32_t *gtab, const int *jtab, float *Y, int64_t ldy, cudaStream_t st) {
-  auto kfn = k_sketch_wht<DERIV, KIND, kCfgWarps, kCfgRowsPerWarp, kCfgPair, kCfgMinBlocks>;
-  constexpr size_t smem = sizeof(WhtSmem<kCfgWarps, kCfgPair, kCfgWarps * kCfgRowsPerWarp>);
+  constexpr bool kDense = KIND == CKINV_DENSE;
+  constexpr int W = kDense ? kDnWarps : kCfgWarps, RPW = kDense ? kDnRowsPerWarp : kCfgRowsPerWarp;
+  constexpr int NR = kDense ? kDnRowsPerWarp : kCfgPair, MINB = kDense ? kDnMinBlocks : kCfgMinBlocks;
+  auto kfn = k_sketch_wht<DERIV, KIND, W, RPW, NR, MINB>;
+  constexpr size_t smem = sizeof(WhtSmem<W, NR, W * RPW, !kDense>);
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  const dim3 grid((unsigned)ceil_div(m, kCfgWarps * kCfgRowsPerWarp));
+  const dim3 grid((unsigned)ceil_div(m, W * RPW));
   note_launch();
-  kfn<<<grid, kCfgWarps * 32, smem, st>>>(n, row0, m, dim, d, nchunks, kp, ps, Kd, ldk, tsg, gsw, gtab, jtab, Y,
-                                          ldy);
+  kfn<<<grid, W * 32, smem, st>>>(n, row0, m, dim, d, nchunks, kp, ps, Kd, ldk, tsg, gsw, gtab, jtab, Y, ldy);
   CK_CUDA(cudaGetLastError());
   return ok();
 }
