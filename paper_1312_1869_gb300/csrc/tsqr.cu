@@ -663,6 +663,11 @@ template <typename T>
 __global__ void __launch_bounds__(SQ_THREADS, sq_min_blocks<T>()) k_sq_step(T *M0, T *Vx0, T *Tm0, T *S0, int d, int q, int nP, int nU,
                                                         int nS, int uw) {
   constexpr int NBS = sq_nb<T>();
+  // launched as a programmatic dependent of the previous step: wait for that grid to complete
+  // (and its writes to be visible), then let the next step's grid be scheduled, so that its
+  // CTAs are resident when this one ends (both are no-ops in an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ __align__(16) uint8_t sm_raw[];
   T *sm = reinterpret_cast<T *>(sm_raw);
   const int H = 2 * d;
@@ -871,6 +876,14 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, bool with_t, cud
   // that stages the panel's reflectors once for several tiles wastes less; with few it is
   // latency bound, and one tile per CTA keeps each CTA short
   const int uw = (sizeof(T) == 8 && P >= 16) ? 4 : 1;
+  // steps after the first start as programmatic dependents (the launch latency between
+  // steps overlaps the previous step); in stream capture, ordinary launches
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK_CUDA(cudaStreamIsCapturing(st, &cap));
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  bool first = true;
   Error e = ok();
   for (int q = 0; q <= npan + 1 && !e.st; ++q) {
     const int j0 = q * NBS, jp = j0 - NBS, jq = j0 - 2 * NBS;
@@ -882,9 +895,16 @@ Error sq_factor(const ckinv_ctx *ctx, const Stage<T> &s, int d, bool with_t, cud
     const int nx = nP + nU + nS + nT;
     if (nx == 0) continue;
     note_launch();
-    k_sq_step<T><<<dim3((unsigned)nx, (unsigned)P), SQ_THREADS, smem, st>>>(s.M, s.Vx, s.Tm, S, d, q, nP, nU, nS,
-                                                                             uw);
-    cudaError_t ce = cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nx, (unsigned)P);
+    cfg.blockDim = dim3(SQ_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = pdl;
+    cfg.numAttrs = (!first && cap == cudaStreamCaptureStatusNone) ? 1 : 0;
+    first = false;
+    cudaError_t ce = cudaLaunchKernelEx(&cfg, k_sq_step<T>, s.M, s.Vx, s.Tm, S, d, q, nP, nU, nS, uw);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
     if (ce != cudaSuccess) e = fail(CKINV_ECUDA, cudaGetErrorString(ce));
   }
   cudaFreeAsync(S, st);
