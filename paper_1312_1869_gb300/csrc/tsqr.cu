@@ -153,19 +153,18 @@ __global__ void __launch_bounds__(PT) k_panel(T *M, T *Vx, T *Tm, int H, int d, 
     }
     block_sum<T, NB, PT>(dots, red, sums);
     // every thread derives the reflector from the reduced norm (no broadcast round trip)
-    // rd = -sign(alpha) normx, head = alpha - rd, tau = (rd - alpha) / rd = 1 + |alpha| / normx
+    // tau = 2 / (v^T v) from the same |x|^2 and 1 / head that form the stored reflector v,
+    // so that tau and v agree to one rounding at the working precision
     const T alpha = x[jj];
     const T sig = sums[jj];
     const T normx = sqrt(alpha * alpha + sig);
     T tau = 0, rd = 0, inv_head = 0;
     if (normx > 0) {
-      const bool neg = alpha < T(0);
-      const T aa = neg ? -alpha : alpha;
-      const T inv_n = T(1) / normx;
-      const T ih = T(1) / (aa + normx);
-      tau = T(1) + aa * inv_n;
-      inv_head = neg ? -ih : ih;
-      rd = neg ? normx : -normx;
+      const T sg = alpha >= 0 ? T(1) : T(-1);
+      const T head = alpha + sg * normx;
+      inv_head = T(1) / head;
+      tau = T(2) / (T(1) + sig * inv_head * inv_head);
+      rd = -sg * normx;
     }
     for (int r = jj + 1 + tid; r < h; r += PT) x[r] *= inv_head;   // this thread's rows only
     if (tid < NB && tid != jj) wv[tid] = Ps[tid * hp + jj] + sums[tid] * inv_head;
