@@ -380,11 +380,14 @@ __global__ void k_wht_masks(const uint32_t *__restrict__ bits, int64_t n, int nc
 
 // The output slots: output j reads U[p_b] at buffer address a_j = (p_b / 32) * 33 + p_b % 32,
 // in bank a_j % 32.  Output j goes to lane bank(a_j), slot = its rank among the outputs of that
-// bank; outputs past the last slot of their bank (rare) fill the empty slots in order.  One CTA.
+// bank; outputs past the last slot of their bank (rare) fill the empty slots in order.  One CTA;
+// one warp ranks the outputs 32 at a time (match masks plus per-bank running counts) and pairs
+// the k-th overflowing output with the k-th empty slot by ballot prefix counts.
 __global__ void k_wht_slots(const int32_t *__restrict__ cols, int d, uint32_t *__restrict__ gtab,
                             int *__restrict__ jtab) {
   __shared__ uint32_t sa[32 * kWMaxU];
   __shared__ int slot[32 * kWMaxU];
+  __shared__ int elist[32 * kWMaxU];
   __shared__ int cnt[32];
   const int nu = (d + 31) / 32;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
@@ -397,32 +400,43 @@ __global__ void k_wht_slots(const int32_t *__restrict__ cols, int d, uint32_t *_
   }
   if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
   __syncthreads();
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const uint32_t bank = sa[j] & 31u;
-    int rank = 0;
-    for (int k = 0; k < j; ++k) rank += (sa[k] & 31u) == bank;
-    slot[j] = rank < nu ? rank * 32 + (int)bank : -1;
-    if (rank < nu) atomicAdd(&cnt[bank], 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // overflow outputs into the empty slots (slot u of lane l is empty iff u >= cnt[l]),
-    // both taken in order; 32 nu >= d slots, so an empty slot is always left
-    int lane = 0, u = 0;
-    for (int j = 0; j < d; ++j) {
-      if (slot[j] >= 0) continue;
-      while (u < nu && u < cnt[lane]) {
-        if (++lane == 32) {
-          lane = 0;
-          ++u;
-        }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    // rank of output j: the outputs of its bank in earlier groups (cnt) and in lower lanes of
+    // its own group; cnt[b] ends as the number of outputs in bank b
+    for (int g = 0; g < d; g += 32) {
+      const int j = g + lane;
+      const bool v = j < d;
+      const uint32_t bank = v ? (sa[j] & 31u) : 32u + (uint32_t)lane;   // lanes past d match none
+      const unsigned peers = __match_any_sync(0xffffffffu, bank);
+      const int base = v ? cnt[bank] : 0;
+      __syncwarp();
+      if (v) {
+        const int rank = base + __popc(peers & lt);
+        slot[j] = rank < nu ? rank * 32 + (int)bank : -1;
+        if ((peers >> lane) == 1u) cnt[bank] = base + __popc(peers);   // the group's last of the bank
       }
-      if (u >= nu) break;
-      slot[j] = u * 32 + lane;
-      if (++lane == 32) {
-        lane = 0;
-        ++u;
-      }
+      __syncwarp();
+    }
+    // the empty slots s = 32 u + l (empty iff u >= cnt[l]), in order of s
+    int ne = 0;
+    for (int g = 0; g < 32 * nu; g += 32) {
+      const bool e = (g >> 5) >= cnt[lane];
+      const unsigned m = __ballot_sync(0xffffffffu, e);
+      if (e) elist[ne + __popc(m & lt)] = g + lane;
+      ne += __popc(m);
+    }
+    __syncwarp();
+    // the k-th overflowing output (in order of j) takes the k-th empty slot: 32 nu >= d leaves
+    // at least as many empty slots as there are overflowing outputs
+    int no = 0;
+    for (int g = 0; g < d; g += 32) {
+      const int j = g + lane;
+      const bool o = j < d && slot[j] < 0;
+      const unsigned m = __ballot_sync(0xffffffffu, o);
+      if (o) slot[j] = elist[no + __popc(m & lt)];
+      no += __popc(m);
     }
   }
   __syncthreads();
