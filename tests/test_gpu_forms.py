@@ -4,7 +4,7 @@ The forms differ in how many BF16 terms carry each kernel entry into the tensor-
 product (BF16: one, about 8 significant bits; BF16x2: two, about 16; BF16x3: three, about
 24, i.e. FP32); accumulation is FP32, Householder leaves FP32, the tree combine, the core
 LUs and the refinement FP64.  X = K_tilde^-1 A amplifies a perturbation of the sketch by
-up to kappa(Y), so each result is judged against
+up to kappa(Y), so each result is checked against
     max(bar, 2 * floor),
 bar = 1e-4 relative (the solve bar) and floor = the oracle re-run at the form's working
 precision: kernel entries rounded the way the form rounds them (unit-variance entries split
